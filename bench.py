@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the local findpts hot path: located + evaluated points/s.
+
+Workload (one step): find + interpolate 10^6 points on the 32^3 hex mesh of
+order 4 (smooth deformation, amplitude 0.3; points uniform in
+[-0.0034, 1.0034]^3), scalar field, all inputs resident on the GPU.  The
+mesh setup (boxes, Psi_L) happens once before timing.  L2 is flushed (a
+256 MB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f64|mixed]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a sample
+
+Under torchrun each rank runs an independent replica on its own GPU with its
+own point set (weak scaling, no collective on the data path); rank 0 prints
+one JSON line with the whole-job throughput (points of all ranks / slowest
+rank's time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "located+evaluated points/s (3D hex p=4)"
+WORKLOAD = "hex3d_32^3_p4_kershaw0.3_1e6pts"
+
+
+def flop_model(stats, N, d, dr, n_found, nc):
+    """Algorithmic FP64 flops (FMA = 2) of one find launch and one eval launch,
+    from the find counters: candidates C, iterations I, beta iterations B."""
+    ne = N ** dr
+    if dr == 3:
+        eval_g = d * 2 * (N * N * (2 * N + 3) + 4 * N) + dr * 8 * N
+        hess = d * 2 * (N * N * (3 * N + 6) + 6 * N) + dr * 12 * N
+        eval_x = 2 * (N ** 3 + N ** 2 + N) + dr * 4 * N
+    else:
+        eval_g = d * 2 * (N * (2 * N + 3)) + dr * 8 * N
+        hess = d * 2 * (N * (3 * N + 6)) + dr * 12 * N
+        eval_x = 2 * (N ** 2 + N) + dr * 4 * N
+    C, I, B = int(stats[0]), int(stats[1]), int(stats[3])
+    box = 2 * d * d + d
+    node = 3 * d * ne
+    newton_alg = 60
+    find = C * (box + node + eval_g) + I * (eval_g + newton_alg) + B * hess
+    ev = n_found * (nc * (eval_x - dr * 4 * N) + dr * 4 * N)
+    return float(find), float(ev)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in Path(self.f.name).read_text().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, nc_field, target_s=10.0):
+    """The FP64 oracle as it stands (brute-force candidates, direct sums,
+    OpenMP over points) on a bounded sample of the same workload."""
+    import oracle
+    om = oracle.OracleMesh(w.coords, w.d, w.dr, w.N)
+    t = time.perf_counter()
+    probe = w.pts[:1000]
+    c, e, r, d2 = om.findpts(probe)
+    om.eval(w.field, c, e, r)
+    dt = time.perf_counter() - t
+    n = int(min(len(w.pts), max(2000, 1000 * target_s / max(dt, 1e-3))))
+    sample = w.pts[:n]
+    t = time.perf_counter()
+    c, e, r, d2 = om.findpts(sample)
+    om.eval(w.field, c, e, r)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {n} points of the workload ({dt:.1f} s): brute-force box test over "
+                      f"all {w.NE} elements + Newton + eval, FP64, OpenMP"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle timed on the host cores."""
+    if rank != 0:
+        return
+    from paper_2501_12349_b300 import workloads as W
+    import oracle
+    w = W.config2()
+    om = oracle.OracleMesh(w.coords, w.d, w.dr, w.N)
+    per_step = 5000
+    ts = []
+    for s in range(args.warmup + args.steps):
+        sl = w.pts[(s * per_step) % len(w.pts):][:per_step]
+        t = time.perf_counter()
+        c, e, r, d2 = om.findpts(sl)
+        om.eval(w.field, c, e, r)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            ts.append(dt)
+    v = per_step * len(ts) / sum(ts)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_points_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": "points/s", "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": f"{per_step} points per step of the 10^6-point workload"},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import paper_2501_12349_b300 as fp
+    from paper_2501_12349_b300 import workloads as W
+
+    w = W.config2(seed=2 + rank)
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    coords = torch.from_numpy(w.coords).to(dev)
+    field = torch.from_numpy(w.field).to(dev)
+    pts = torch.from_numpy(w.pts).to(dev)
+    n = pts.shape[0]
+    t0 = time.perf_counter()
+    mesh = fp.Mesh(coords, 3, 3, w.order, precision=fp.FP_MIXED if args.precision == "mixed" else fp.FP_F64)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    code = torch.empty(n, dtype=torch.int32, device=dev)
+    elem = torch.empty(n, dtype=torch.int32, device=dev)
+    r = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    dist2 = torch.empty(n, dtype=torch.float64, device=dev)
+    out = torch.empty((1, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        fp.fp_findpts(mesh.handle, pts, code, elem, r, dist2)
+        fp.fp_eval(mesh.handle, code, elem, r, field, 1, out)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(st)
+        fp.fp_findpts(mesh.handle, pts, code, elem, r, dist2)
+        ev[s][1].record(st)
+        fp.fp_eval(mesh.handle, code, elem, r, field, 1, out)
+        ev[s][2].record(st)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    find_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
+    eval_ms = [ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)]
+    step_ms = [a + b for a, b in zip(find_ms, eval_ms)]
+    t_local = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_local], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_local
+    value = world * n * args.steps / t_max
+
+    # counters for the algorithmic flop count (untimed)
+    stats = torch.zeros(fp.FP_NSTATS, dtype=torch.int64, device=dev)
+    fp.fp_findpts_stats(mesh.handle, pts, code, elem, r, dist2, stats)
+    sv = stats.cpu().numpy()
+    n_found = int((code != 2).sum().item())
+    fl_find, fl_eval = flop_model(sv, w.N, 3, 3, n_found, 1)
+    peak64 = fp.fp_alu_peak(0, 4000) / 1e3  # TFLOP/s
+    find_avg = statistics.mean(find_ms) / 1e3
+    eval_avg = statistics.mean(eval_ms) / 1e3
+    ach = fl_find / find_avg / 1e12
+
+    # end to end through host buffers: pinned H2D of the points, find + eval,
+    # D2H of code, elem, r, dist2 and the interpolated values
+    hp = torch.from_numpy(w.pts).pin_memory()
+    hc = torch.empty(n, dtype=torch.int32).pin_memory()
+    he = torch.empty(n, dtype=torch.int32).pin_memory()
+    hr = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    hd = torch.empty(n, dtype=torch.float64).pin_memory()
+    hu = torch.empty((1, n), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        pts.copy_(hp, non_blocking=True)
+        step()
+        for h_, d_ in ((hc, code), (he, elem), (hr, r), (hd, dist2), (hu, out)):
+            h_.copy_(d_, non_blocking=True)
+        b.record(st)
+        b.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    h2d = n * 3 * 8
+    d2h = n * (4 + 4 + 24 + 8 + 8)
+    e2e_t = sum(e2e_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    e2e_v = world * n * args.steps / e2e_t
+    status = mesh.device_status()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, 1)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "f64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points_per_gpu": n, "precision": args.precision,
+                       "nc": 1, "l2": "flushed (256 MB write) before each timed step",
+                       "parallelism": f"replicas{world}"},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
+                         "frac": ach / peak64, "traffic": None, "kernel": "k_find_f64",
+                         "peak_source": "FP64 FMA pipe, measured live by fp_alu_peak (no FP64 entry in MEASURED_PEAKS.json)"},
+            "kernels_ms": {"find": statistics.mean(find_ms), "eval": statistics.mean(eval_ms)},
+            "eval_roofline": {"bound": "alu", "achieved": fl_eval / eval_avg / 1e12, "peak": peak64,
+                              "unit": "TFLOP/s", "frac": fl_eval / eval_avg / 1e12 / peak64},
+            "find_counters": {"candidates": int(sv[0]), "iterations": int(sv[1]), "rejected": int(sv[2]),
+                              "beta_iterations": int(sv[3]), "per_point_iterations": float(sv[1]) / n},
+            "setup_ms": setup_ms, "wall_s_timed": wall, "device_status": status,
+            "e2e": {"value": e2e_v, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

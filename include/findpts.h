@@ -1,0 +1,168 @@
+/*
+ * findpts.h — C ABI of libfindpts, a B300 (sm_103a) implementation of local
+ * point location and field evaluation in high-order curvilinear meshes
+ * (Mittal et al., "General Field Evaluation in High-Order Meshes on GPUs",
+ * arXiv 2501.12349).
+ *
+ * Method, by the paper's sections:
+ *   Setup (Sec. 3.1): per element, an axis-aligned bounding box (Sec. 3.1.1,
+ *     Eqs. 1D_bases_bounds, 1D_bound_final, 2D_function_bound, AABB_test) and
+ *     an oriented bounding box (Sec. 3.1.2, Eqs. OBB_transformation, OBB_test),
+ *     then the process-local Cartesian map Psi_L from a grid cell to the
+ *     elements whose AABB covers it (Sec. 3.1.3).
+ *   Find (Sec. 3.2): cell lookup, box filter, trust-region Newton on
+ *     f(r) = 0.5 |x* - x(r)|^2 (Sec. 3.2.1, Eqs. newton, newton_jacobian,
+ *     newton_hessian), candidate selection (first INTERIOR, else the BORDER
+ *     with the smallest distance).
+ *   Interpolate (Sec. 3.3, Eq. u_tensor).
+ *   Surface meshes (Sec. 4): quadrilaterals embedded in 3D.
+ * The multi-rank stages (global map Psi_G, Sec. 3.1.4, and point routing)
+ * have no counterpart: one process drives one GPU.
+ *
+ * Conventions shared by every call:
+ *   d  = physical dimension (2 or 3), dr = reference dimension (dr == d for
+ *        quads and hexes, dr = 2, d = 3 for surface quads), N = order + 1
+ *        (2 <= N <= FP_MAX_N), ne = N^dr nodes per element.
+ *   Node index within an element is lexicographic with r fastest:
+ *        n = i + N*j (+ N*N*k), node (i,j,k) sits at GLL reference point
+ *        (zeta_i, zeta_j, zeta_k).
+ *   Coordinates and fields are structure-of-arrays: coords[c][e][n] at
+ *        offset (c*NE + e)*ne + n.  Points are array-of-structures:
+ *        pts[p][c] at offset p*d + c.
+ *   Array arguments of find / eval are DEVICE memory owned by the caller
+ *        unless stated otherwise.
+ *   `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *        asynchronous on that stream unless stated otherwise; the caller
+ *        keeps every buffer alive until the stream has passed the call.
+ *   Return value: FP_OK (0) or a negative FP_E* status; no call throws, and
+ *        per-point outcomes are reported in `code`, never as a status.
+ */
+#ifndef FINDPTS_H
+#define FINDPTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FP_OK 0
+#define FP_EINVAL (-1)       /* bad argument (NULL pointer, size, dimension) */
+#define FP_ENOMEM (-2)       /* device allocation failed or budget exceeded  */
+#define FP_ELAUNCH (-3)      /* a kernel launch or CUDA runtime call failed  */
+#define FP_EDEVICE (-4)      /* a kernel set its device status word          */
+#define FP_ETIMEDOUT (-5)    /* a host-side wait ran out                      */
+#define FP_EBUSY (-6)        /* resource in use                               */
+#define FP_EUNSUPPORTED (-7) /* element type / order not built               */
+
+/* ---- per-point location codes (Sec. 3.2, the enum c*) ------------------- */
+#define FP_INTERIOR 0
+#define FP_BORDER 1
+#define FP_NOT_FOUND 2
+
+/* ---- arithmetic of the find kernels ------------------------------------- */
+#define FP_F64 0   /* every step in FP64                                        */
+#define FP_MIXED 1 /* FP32 box filter and early Newton steps; FP64 final steps,  */
+                   /* residual check and ill-conditioned Jacobian solves         */
+
+#define FP_MAX_N 8 /* orders 1..7 */
+
+typedef struct fp_mesh_s* fp_mesh; /* opaque; library-owned; device-resident */
+
+/* Options of Setup and Find.  fp_opts_default fills the paper's defaults. */
+typedef struct {
+  double bbox_tol;   /* box expansion, fraction of the extent (Sec. 3.1.1: 10%)    */
+  int M;             /* Chebyshev interval points of the bounds; 0 => 2N (3.1.1)   */
+  int n_grid;        /* cells per direction of Psi_L; 0 => smallest n, n^d >= NE   */
+  double newton_tol; /* stop when |dr|_inf < newton_tol (Sec. 3.2.1: 1e-10)        */
+  int max_iter;      /* Newton iteration cap per candidate (Sec. 3.2.1: 50)        */
+  double dist_tol;   /* surfaces: INTERIOR needs dist2 < dist_tol (Sec. 4.4: 1e-10) */
+  int precision;     /* FP_F64 or FP_MIXED                                          */
+} fp_opts;
+
+void fp_opts_default(fp_opts* opts);
+
+/* Setup (Sec. 3.1).  Copies coords_dev ([d][NE][N^dr] FP64, device) into
+ * library-owned device memory, computes element AABBs and OBBs expanded by
+ * bbox_tol and builds Psi_L, all on the GPU.  Blocks until done (it
+ * allocates).  *out receives the handle; fp_free releases it.
+ * Errors: FP_EINVAL for a bad dimension pair, order, NE <= 0 or M outside
+ * [2, 32]; FP_EUNSUPPORTED for N > FP_MAX_N; FP_ENOMEM; FP_ELAUNCH. */
+int fp_setup(const double* coords_dev, int d, int dr, int order, int64_t NE,
+             const fp_opts* opts, void* stream, fp_mesh* out);
+
+/* Releases every device allocation of the mesh (synchronises the device). */
+int fp_free(fp_mesh m);
+
+/* Selects the arithmetic of later fp_findpts calls on this mesh: FP_F64 or
+ * FP_MIXED (both sets of device data are built by fp_setup).  Host call. */
+int fp_set_precision(fp_mesh m, int precision);
+
+/* Find (Sec. 3.2) for n points pts_dev ([n][d] FP64).  Outputs (device):
+ *   code[n]  FP_INTERIOR / FP_BORDER / FP_NOT_FOUND
+ *   elem[n]  element id, -1 when NOT_FOUND
+ *   r[n][dr] reference coordinates in [-1,1]^dr, 0 when NOT_FOUND
+ *   dist2[n] |x* - x(r*)|^2, +inf when NOT_FOUND
+ * A point with a non-finite coordinate is NOT_FOUND.  n == 0 is a no-op.
+ * Errors: FP_EINVAL (NULL pointer with n > 0, n < 0), FP_ELAUNCH. */
+int fp_findpts(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
+               int32_t* elem, double* r, double* dist2, void* stream);
+
+/* As fp_findpts, and adds this call's counters into stats_dev (device,
+ * FP_NSTATS uint64 values, caller-zeroed):
+ *   [0] candidates that passed the box filter  [1] Newton iterations
+ *   [2] rejected trust-region steps            [3] iterations with beta = 1
+ *   [4] FP64 iterations of the mixed path      [5] candidates rechecked in FP64 */
+#define FP_NSTATS 8
+int fp_findpts_stats(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
+                     int32_t* elem, double* r, double* dist2, uint64_t* stats_dev,
+                     void* stream);
+
+/* Interpolate (Sec. 3.3): out[c][p] = u_c(r_p) in element elem_p for the
+ * nc components of field_dev ([nc][NE][N^dr] FP64, device, same node layout
+ * as the coordinates); 0 where code == FP_NOT_FOUND.  The same find output
+ * serves any number of fields.  Errors: FP_EINVAL, FP_ELAUNCH. */
+int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
+            int64_t n, const double* field_dev, int nc, double* out, void* stream);
+
+/* ---- introspection (tests, benchmarks) ----------------------------------- */
+typedef struct {
+  int d, dr, N, M, n_grid;
+  int64_t NE, n_cells, n_cell_entries;
+  double grid_lo[3], grid_hi[3];
+  size_t device_bytes;
+} fp_mesh_info;
+
+/* Host call; fills *info. */
+int fp_get_info(fp_mesh m, fp_mesh_info* info);
+
+/* Copies the boxes into caller device buffers (any may be NULL):
+ * aabb[NE][2d] = (lo_0..lo_{d-1}, hi_0..hi_{d-1}), already expanded;
+ * obb_c[NE][d] the OBB centre; obb_A[NE][d][d] (row-major) the map A with
+ * |A (x - c)|_inf <= 1 exactly on the expanded OBB.  Synchronous. */
+int fp_get_boxes(fp_mesh m, double* aabb, double* obb_c, double* obb_A, void* stream);
+
+/* Copies Psi_L in CSR form into caller device buffers: cell_start[n_cells+1],
+ * cell_elems[n_cell_entries], element ids ascending within a cell.  Cell
+ * (c_0,c_1,c_2) has index c_0 + n_grid*(c_1 + n_grid*c_2).  Synchronous. */
+int fp_get_grid(fp_mesh m, int32_t* cell_start, int32_t* cell_elems, void* stream);
+
+/* Reads and clears the mesh's device status word: 0, or the first error a
+ * kernel recorded (an out-of-range element or cell index).  Synchronises
+ * the stream. */
+int fp_device_status(fp_mesh m, int* status, void* stream);
+
+const char* fp_status_string(int status);
+
+/* Measured FMA-pipe throughput in GFLOP/s (1 FMA = 2 flop): which = 0 FP64,
+ * 1 FP32.  The roofline denominator of the find / eval kernels, which are
+ * bound by these pipes.  Allocates a small scratch buffer; synchronous. */
+int fp_alu_peak(int which, int iters, double* gflops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FINDPTS_H */

@@ -1,0 +1,261 @@
+"""B300-native local findpts (arXiv 2501.12349): Python binding of libfindpts.
+
+Thin ctypes marshalling over the C ABI declared in include/findpts.h: every
+function below has the C function's name, passes device pointers of torch
+CUDA tensors and the current CUDA stream, and raises FindptsError on a
+non-zero status.  All arithmetic runs in the library's CUDA kernels; there is
+no CPU fallback — importing works without a GPU, but calls need the built
+libfindpts.so and a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libfindpts.so"
+
+FP_OK, FP_EINVAL, FP_ENOMEM, FP_ELAUNCH, FP_EDEVICE, FP_ETIMEDOUT, FP_EBUSY, FP_EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+FP_INTERIOR, FP_BORDER, FP_NOT_FOUND = 0, 1, 2
+FP_F64, FP_MIXED = 0, 1
+FP_MAX_N = 8
+FP_NSTATS = 8
+
+
+class FindptsError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {status} ({fp_status_string(status)})")
+        self.status = status
+
+
+class FpOpts(ctypes.Structure):
+    _fields_ = [("bbox_tol", ctypes.c_double), ("M", ctypes.c_int), ("n_grid", ctypes.c_int),
+                ("newton_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("dist_tol", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class FpMeshInfo(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("dr", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int),
+                ("n_grid", ctypes.c_int), ("NE", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("n_cell_entries", ctypes.c_int64), ("grid_lo", ctypes.c_double * 3),
+                ("grid_hi", ctypes.c_double * 3), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libfindpts.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2501_12349_b300._build`")
+        L = ctypes.CDLL(str(LIB_PATH))
+        sig = {
+            "fp_opts_default": ([ctypes.POINTER(FpOpts)], None),
+            "fp_setup": ([_vp, _int, _int, _int, _i64, ctypes.POINTER(FpOpts), _vp, ctypes.POINTER(_vp)], _int),
+            "fp_free": ([_vp], _int),
+            "fp_set_precision": ([_vp, _int], _int),
+            "fp_findpts": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _int),
+            "fp_findpts_stats": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
+            "fp_eval": ([_vp, _vp, _vp, _vp, _i64, _vp, _int, _vp, _vp], _int),
+            "fp_get_info": ([_vp, ctypes.POINTER(FpMeshInfo)], _int),
+            "fp_get_boxes": ([_vp, _vp, _vp, _vp, _vp], _int),
+            "fp_get_grid": ([_vp, _vp, _vp, _vp], _int),
+            "fp_device_status": ([_vp, ctypes.POINTER(_int), _vp], _int),
+            "fp_status_string": ([_int], ctypes.c_char_p),
+            "fp_alu_peak": ([_int, _int, ctypes.POINTER(ctypes.c_double), _vp], _int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def fp_status_string(status: int) -> str:
+    return lib().fp_status_string(int(status)).decode()
+
+
+def _check(fn: str, status: int) -> None:
+    if status != FP_OK:
+        raise FindptsError(fn, status)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return _vp(t.data_ptr())
+
+
+def fp_opts_default() -> FpOpts:
+    o = FpOpts()
+    lib().fp_opts_default(ctypes.byref(o))
+    return o
+
+
+def fp_setup(coords, d: int, dr: int, order: int, opts: FpOpts | None = None, stream=None) -> _vp:
+    """Setup (Sec. 3.1) from device coordinates [d][NE][N^dr] (float64)."""
+    import torch
+    NE = coords.numel() // (d * (order + 1) ** dr)
+    h = _vp()
+    rc = lib().fp_setup(_ptr(coords, torch.float64, "coords"), d, dr, order, NE,
+                        ctypes.byref(opts) if opts is not None else None, _stream(stream), ctypes.byref(h))
+    _check("fp_setup", rc)
+    return h
+
+
+def fp_free(mesh) -> None:
+    _check("fp_free", lib().fp_free(mesh))
+
+
+def fp_set_precision(mesh, precision: int) -> None:
+    _check("fp_set_precision", lib().fp_set_precision(mesh, int(precision)))
+
+
+def fp_findpts(mesh, pts, code, elem, r, dist2, stream=None) -> None:
+    import torch
+    n = pts.shape[0] if pts.dim() > 0 else 0
+    _check("fp_findpts", lib().fp_findpts(
+        mesh, _ptr(pts, torch.float64, "pts"), n, _ptr(code, torch.int32, "code"),
+        _ptr(elem, torch.int32, "elem"), _ptr(r, torch.float64, "r"),
+        _ptr(dist2, torch.float64, "dist2"), _stream(stream)))
+
+
+def fp_findpts_stats(mesh, pts, code, elem, r, dist2, stats, stream=None) -> None:
+    import torch
+    n = pts.shape[0] if pts.dim() > 0 else 0
+    _check("fp_findpts_stats", lib().fp_findpts_stats(
+        mesh, _ptr(pts, torch.float64, "pts"), n, _ptr(code, torch.int32, "code"),
+        _ptr(elem, torch.int32, "elem"), _ptr(r, torch.float64, "r"),
+        _ptr(dist2, torch.float64, "dist2"), _ptr(stats, torch.int64, "stats"), _stream(stream)))
+
+
+def fp_eval(mesh, code, elem, r, field, nc: int, out, stream=None) -> None:
+    import torch
+    n = code.shape[0]
+    _check("fp_eval", lib().fp_eval(
+        mesh, _ptr(code, torch.int32, "code"), _ptr(elem, torch.int32, "elem"),
+        _ptr(r, torch.float64, "r"), n, _ptr(field, torch.float64, "field"), int(nc),
+        _ptr(out, torch.float64, "out"), _stream(stream)))
+
+
+def fp_get_info(mesh) -> FpMeshInfo:
+    info = FpMeshInfo()
+    _check("fp_get_info", lib().fp_get_info(mesh, ctypes.byref(info)))
+    return info
+
+
+def fp_get_boxes(mesh, aabb, obb_c, obb_A, stream=None) -> None:
+    import torch
+    _check("fp_get_boxes", lib().fp_get_boxes(mesh, _ptr(aabb, torch.float64), _ptr(obb_c, torch.float64),
+                                              _ptr(obb_A, torch.float64), _stream(stream)))
+
+
+def fp_get_grid(mesh, cell_start, cell_elems, stream=None) -> None:
+    import torch
+    _check("fp_get_grid", lib().fp_get_grid(mesh, _ptr(cell_start, torch.int32), _ptr(cell_elems, torch.int32),
+                                            _stream(stream)))
+
+
+def fp_device_status(mesh, stream=None) -> int:
+    s = _int(0)
+    _check("fp_device_status", lib().fp_device_status(mesh, ctypes.byref(s), _stream(stream)))
+    return s.value
+
+
+def fp_alu_peak(which: int, iters: int = 4000, stream=None) -> float:
+    g = ctypes.c_double(0.0)
+    _check("fp_alu_peak", lib().fp_alu_peak(int(which), int(iters), ctypes.byref(g), _stream(stream)))
+    return g.value
+
+
+class Mesh:
+    """Owns an fp_mesh handle; allocates outputs as torch tensors."""
+
+    def __init__(self, coords, d: int, dr: int, order: int, stream=None, **opts):
+        o = fp_opts_default()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.d, self.dr, self.order = d, dr, order
+        self.N = order + 1
+        self.NE = coords.numel() // (d * self.N ** dr)
+        self.handle = fp_setup(coords, d, dr, order, o, stream)
+
+    def close(self):
+        if self.handle is not None:
+            fp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: int):
+        fp_set_precision(self.handle, precision)
+
+    def find(self, pts, stream=None, stats=None):
+        import torch
+        n = pts.shape[0]
+        dev = pts.device
+        code = torch.empty(n, dtype=torch.int32, device=dev)
+        elem = torch.empty(n, dtype=torch.int32, device=dev)
+        r = torch.empty((n, self.dr), dtype=torch.float64, device=dev)
+        dist2 = torch.empty(n, dtype=torch.float64, device=dev)
+        if stats is None:
+            fp_findpts(self.handle, pts, code, elem, r, dist2, stream)
+        else:
+            fp_findpts_stats(self.handle, pts, code, elem, r, dist2, stats, stream)
+        return code, elem, r, dist2
+
+    def eval(self, code, elem, r, field, stream=None):
+        import torch
+        nc = field.numel() // (self.NE * self.N ** self.dr)
+        out = torch.empty((nc, code.shape[0]), dtype=torch.float64, device=code.device)
+        fp_eval(self.handle, code, elem, r, field, nc, out, stream)
+        return out
+
+    def info(self) -> FpMeshInfo:
+        return fp_get_info(self.handle)
+
+    def boxes(self):
+        import torch
+        dev = torch.device("cuda")
+        aabb = torch.empty((self.NE, 2 * self.d), dtype=torch.float64, device=dev)
+        oc = torch.empty((self.NE, self.d), dtype=torch.float64, device=dev)
+        oA = torch.empty((self.NE, self.d, self.d), dtype=torch.float64, device=dev)
+        fp_get_boxes(self.handle, aabb, oc, oA)
+        return aabb, oc, oA
+
+    def grid(self):
+        import torch
+        info = self.info()
+        cs = torch.empty(info.n_cells + 1, dtype=torch.int32, device="cuda")
+        ce = torch.empty(max(info.n_cell_entries, 1), dtype=torch.int32, device="cuda")
+        fp_get_grid(self.handle, cs, ce)
+        return cs, ce[:info.n_cell_entries]
+
+    def device_status(self) -> int:
+        return fp_device_status(self.handle)

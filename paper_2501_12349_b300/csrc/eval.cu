@@ -1,0 +1,55 @@
+// Interpolate (Sec. 3.3, Eq. u_tensor): u(r*) in element e* for each found
+// point, one thread per point, the contraction sum-factorised (N^3 + N^2 + N
+// FMA per component for a hex).  FP64-pipe bound like find.
+#include "fp_basis.cuh"
+#include "fp_common.cuh"
+
+namespace fp {
+
+constexpr int kEvalThreads = 128;
+
+template <int N, int DR>
+__global__ void __launch_bounds__(kEvalThreads)
+    k_eval_f64(const BasisTab B, const int* __restrict__ code, const int* __restrict__ elem,
+               const double* __restrict__ r, int64_t n, const double* __restrict__ field, int nc,
+               int64_t NE, double* __restrict__ out, int* status) {
+  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  const int64_t cs = NE * NN;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int c0 = __ldg(code + p), e = __ldg(elem + p);
+    const bool valid = c0 != FP_NOT_FOUND && e >= 0 && e < NE;
+    if (c0 != FP_NOT_FOUND && !valid) record_status(status, FP_DEV_BAD_ELEM);
+    if (!valid) {
+      for (int c = 0; c < nc; ++c) out[(int64_t)c * n + p] = 0.0;
+      continue;
+    }
+    double ph[DR][N], dph[DR][N];
+#pragma unroll
+    for (int j = 0; j < DR; ++j) lagrange<N, double>(B.z, B.w, __ldg(r + p * DR + j), ph[j], dph[j]);
+    for (int c = 0; c < nc; ++c) {
+      double v;
+      map_eval<N, DR, 1, false, double>(field + c * cs + (int64_t)e * NN, 0, ph, dph, &v, nullptr);
+      out[(int64_t)c * n + p] = v;
+    }
+  }
+}
+
+}  // namespace fp
+
+extern "C" int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
+                       int64_t n, const double* field, int nc, double* out, void* stream) {
+  using namespace fp;
+  if (!m || n < 0 || nc < 0) return FP_EINVAL;
+  if (n == 0 || nc == 0) return FP_OK;
+  if (!code || !elem || !r || !field || !out) return FP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  return dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+    constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;
+    (void)Dc;
+    const int blocks = grid_for(n, kEvalThreads, 148 * 64);
+    k_eval_f64<N, DR><<<blocks, kEvalThreads, 0, st>>>(m->basis, code, elem, r, n, field, nc, m->NE,
+                                                        out, m->status);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+  });
+}

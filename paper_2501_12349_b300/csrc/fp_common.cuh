@@ -1,0 +1,141 @@
+// Internal definitions of libfindpts shared by its translation units (not
+// part of the C ABI): status helpers, the mesh object, the by-value views
+// the kernels receive, and the grid-cell map of Psi_L.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "findpts.h"
+
+#define FP_CUDA_TRY(expr)                                                  \
+  do {                                                                     \
+    cudaError_t _e = (expr);                                               \
+    if (_e != cudaSuccess) {                                               \
+      return _e == cudaErrorMemoryAllocation ? FP_ENOMEM : FP_ELAUNCH;     \
+    }                                                                      \
+  } while (0)
+
+#define FP_TRY(expr)            \
+  do {                          \
+    int _s = (expr);            \
+    if (_s != FP_OK) return _s; \
+  } while (0)
+
+// Device status word values.  A kernel never traps: it records the first
+// error here and skips the offending access.
+#define FP_DEV_BAD_ELEM 1  // an element id outside [0, NE) was read from Psi_L
+#define FP_DEV_BAD_CELL 2  // a cell index outside the grid was formed
+#define FP_DEV_SPIN_CAP 3  // a bounded device wait gave up
+#define FP_DEV_BAD_ITEM 4  // a work item outside its table was read
+#define FP_DEV_DEGENERATE 5  // an element's Jacobian at its centre is singular
+
+namespace fp {
+
+// GLL nodes z_i and barycentric weights w_i = 1 / prod_{m!=i} (z_i - z_m) of
+// one order, passed by value so the kernels read them from the constant bank.
+struct BasisTab {
+  double z[FP_MAX_N];
+  double w[FP_MAX_N];
+  float zf[FP_MAX_N];
+  float wf[FP_MAX_N];
+};
+
+// Everything a find / eval kernel reads about a mesh (passed by value).
+struct DevMesh {
+  const double* coords;    // [d][NE][ne]
+  const float* coords32;   // FP32 copy (mixed path)
+  const double* aabb;      // [NE][2d], expanded
+  const double* obb_c;     // [NE][d]
+  const double* obb_A;     // [NE][d][d]
+  const float* box32;      // [NE][BOX32_STRIDE]: outward-rounded FP32 boxes (mixed path)
+  const int* cell_start;   // [ncell + 1]
+  const int* cell_elems;   // [nnz]
+  int64_t NE;
+  int64_t cstride;         // NE * ne: distance between coordinate components
+  double lo[3], hi[3], scale[3];
+  int NL;
+  int max_iter;
+  double newton_tol;
+  double dist_tol;
+  int* status;
+};
+
+// The Psi_L cell coordinate of x along one axis (Sec. 3.1.3): floor of
+// (x - lo) * scale, clamped to [0, NL-1].  The same rounded operations serve
+// the element corners at setup and the points at find, so x inside an AABB
+// implies x's cell lies in the element's cell range.
+__device__ __forceinline__ int cell_coord(double x, double lo, double scale, int NL) {
+  double t = __dmul_rn(__dsub_rn(x, lo), scale);
+  int c = (t >= (double)NL) ? NL - 1 : (int)floor(t);
+  return c < 0 ? 0 : c;
+}
+
+__device__ __forceinline__ void record_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace fp
+
+// The library-owned mesh object behind the fp_mesh handle.
+struct fp_mesh_s {
+  int d, dr, N, ne, M, NL;
+  int64_t NE, ncell, nnz;
+  fp_opts opts;
+  int precision;
+  double* coords;
+  float* coords32;
+  double* aabb;
+  double* obb_c;
+  double* obb_A;
+  float* box32;
+  int* cell_start;
+  int* cell_elems;
+  int* status;
+  double lo[3], hi[3], scale[3];
+  size_t bytes;
+  fp::BasisTab basis;
+  fp::DevMesh view() const;
+};
+
+namespace fp {
+// host helpers shared by the translation units
+int host_basis_tab(int N, BasisTab* tab);
+int check_mesh(const fp_mesh_s* m);
+}  // namespace fp
+
+#include <type_traits>
+
+namespace fp {
+
+template <int V>
+using ic = std::integral_constant<int, V>;
+
+// Calls f(ic<N>, ic<D>, ic<DR>) for the element shapes the library is built
+// for: N in 2..FP_MAX_N and (d, dr) in {(2,2), (3,3), (3,2)}.
+template <typename F>
+int dispatch_shape(int N, int d, int dr, F&& f) {
+  auto withN = [&](auto Dc, auto DRc) -> int {
+    switch (N) {
+      case 2: return f(ic<2>{}, Dc, DRc);
+      case 3: return f(ic<3>{}, Dc, DRc);
+      case 4: return f(ic<4>{}, Dc, DRc);
+      case 5: return f(ic<5>{}, Dc, DRc);
+      case 6: return f(ic<6>{}, Dc, DRc);
+      case 7: return f(ic<7>{}, Dc, DRc);
+      case 8: return f(ic<8>{}, Dc, DRc);
+      default: return FP_EUNSUPPORTED;
+    }
+  };
+  if (d == 2 && dr == 2) return withN(ic<2>{}, ic<2>{});
+  if (d == 3 && dr == 3) return withN(ic<3>{}, ic<3>{});
+  if (d == 3 && dr == 2) return withN(ic<3>{}, ic<2>{});
+  return FP_EINVAL;
+}
+
+inline int grid_for(int64_t n, int threads, int max_blocks) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < max_blocks ? b : max_blocks);
+}
+
+}  // namespace fp

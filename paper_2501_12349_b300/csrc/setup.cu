@@ -1,0 +1,871 @@
+// Setup (Sec. 3.1): element boxes and the process-local map Psi_L, on the GPU.
+//
+// Host side: the per-order constant tables (GLL nodes, barycentric and
+// quadrature weights, Chebyshev points, piecewise-linear basis bounds and
+// their pairwise products).  Device side: one CTA per element computes its
+// AABB and OBB (k_boxes); four small kernels build Psi_L in CSR form.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fp_basis.cuh"
+#include "fp_common.cuh"
+
+namespace fp {
+
+namespace {
+
+constexpr int kMaxM = 32;
+
+// ---- host tables ----------------------------------------------------------
+
+// P_n(x) and P'_n(x) by the three-term recurrence.
+void legendre_host(int n, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  // (1 - x^2) P'_n = n (P_{n-1} - x P_n), valid away from +-1
+  *dP = (fabs(x) < 1.0) ? n * (p0 - x * p1) / (1.0 - x * x) : 0.5 * n * (n + 1) * pow(x, n + 1);
+}
+
+// GLL nodes: +-1 and the extrema of P_{N-1}, by Newton on P'_{N-1} with
+// P'' taken from Legendre's equation (1-x^2) P'' = 2x P' - n(n+1) P.
+// Also the GLL quadrature weights 2 / (n (n+1) P_n(z)^2).
+void gll_host(int N, double* z, double* wq) {
+  const int n = N - 1;
+  z[0] = -1.0;
+  z[N - 1] = 1.0;
+  for (int j = 1; j < N - 1; ++j) {
+    double x = -cos(M_PI * j / n);
+    for (int it = 0; it < 60; ++it) {
+      double P, dP;
+      legendre_host(n, x, &P, &dP);
+      const double d2P = (2.0 * x * dP - n * (n + 1.0) * P) / (1.0 - x * x);
+      const double step = dP / d2P;
+      x -= step;
+      if (fabs(step) < 1e-17) break;
+    }
+    z[j] = x;
+  }
+  for (int j = 0; j < N; ++j) {
+    double P, dP;
+    legendre_host(n, z[j], &P, &dP);
+    wq[j] = 2.0 / (n * (n + 1.0) * P * P);
+  }
+}
+
+// phi_i(x) and phi'_i(x) with barycentric weights wb (product form).
+void lagrange_host(int N, const double* z, const double* wb, double x, double* phi, double* dphi) {
+  for (int i = 0; i < N; ++i) {
+    double p = 1.0, dp = 0.0;
+    for (int m = 0; m < N; ++m) {
+      if (m == i) continue;
+      dp = dp * (x - z[m]) + p;
+      p = p * (x - z[m]);
+    }
+    phi[i] = wb[i] * p;
+    dphi[i] = wb[i] * dp;
+  }
+}
+
+}  // namespace
+
+int host_basis_tab(int N, BasisTab* tab) {
+  if (N < 2 || N > FP_MAX_N) return FP_EUNSUPPORTED;
+  double z[FP_MAX_N], wq[FP_MAX_N];
+  gll_host(N, z, wq);
+  memset(tab, 0, sizeof(*tab));
+  for (int i = 0; i < N; ++i) {
+    double p = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != i) p *= (z[i] - z[m]);
+    tab->z[i] = z[i];
+    tab->w[i] = 1.0 / p;
+    tab->zf[i] = (float)z[i];
+    tab->wf[i] = (float)(1.0 / p);
+  }
+  return FP_OK;
+}
+
+namespace {
+
+// Device table layout (doubles) for the box kernel.
+struct TabLayout {
+  int N, M;
+  int c0, c1, eta, vlo, vhi, pmin, pmax, total;
+  __host__ __device__ TabLayout(int N_, int M_) : N(N_), M(M_) {
+    c0 = 0;
+    c1 = c0 + N;
+    eta = c1 + N;
+    vlo = eta + M;
+    vhi = vlo + N * M;
+    pmin = vhi + N * M;
+    pmax = pmin + M * M * N * N;
+    total = pmax + M * M * N * N;
+  }
+};
+
+// Sec. 3.1.1 tables for (N, M):
+//  c0, c1: a_l = sum_i c_l[i] u_i, the (2l+1)/2-scaled Legendre projections,
+//    from GLL quadrature (exact: phi_i P_l has degree <= N <= 2N-3 for N >= 3;
+//    closed form for N = 2);
+//  eta: Chebyshev points (Eq. chebyshev);
+//  vlo, vhi [i][j]: basis bounds of Eq. 1D_bases_bounds, tangents at the
+//    interval midpoints evaluated at their distance from eta_j;
+//  pmin, pmax [k][l][b][a]: min / max of the four products of the bound
+//    values of basis a at eta_k and basis b at eta_l, so that the four-term
+//    min of Eq. 2D_function_bound_1 is w * pmin when w >= 0, w * pmax else.
+std::vector<double> bound_tables(int N, int M) {
+  TabLayout L(N, M);
+  std::vector<double> t(L.total, 0.0);
+  double z[FP_MAX_N], wq[FP_MAX_N], wb[FP_MAX_N];
+  gll_host(N, z, wq);
+  for (int i = 0; i < N; ++i) {
+    double p = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != i) p *= (z[i] - z[m]);
+    wb[i] = 1.0 / p;
+  }
+  for (int i = 0; i < N; ++i) {
+    t[L.c0 + i] = 0.5 * wq[i];
+    t[L.c1 + i] = (N == 2) ? (i == 0 ? -0.5 : 0.5) : 1.5 * wq[i] * z[i];
+  }
+  double eta[kMaxM];
+  for (int j = 0; j < M; ++j) eta[j] = -cos(M_PI * (double)j / (double)(M - 1));
+  for (int j = 0; j < M; ++j) t[L.eta + j] = eta[j];
+  for (int j = 0; j < M; ++j) {
+    double phi[FP_MAX_N], dphi[FP_MAX_N], pm[FP_MAX_N], dpm[FP_MAX_N], pp[FP_MAX_N], dpp[FP_MAX_N];
+    if (j == 0 || j == M - 1) {
+      for (int i = 0; i < N; ++i) {
+        const double v = (j == 0) ? (i == 0) : (i == N - 1);
+        t[L.vlo + i * M + j] = v;
+        t[L.vhi + i * M + j] = v;
+      }
+      continue;
+    }
+    const double xm = 0.5 * (eta[j - 1] + eta[j]), xp = 0.5 * (eta[j] + eta[j + 1]);
+    lagrange_host(N, z, wb, eta[j], phi, dphi);
+    lagrange_host(N, z, wb, xm, pm, dpm);
+    lagrange_host(N, z, wb, xp, pp, dpp);
+    for (int i = 0; i < N; ++i) {
+      const double cand[3] = {phi[i], pm[i] + (eta[j] - xm) * dpm[i], pp[i] - (xp - eta[j]) * dpp[i]};
+      t[L.vlo + i * M + j] = std::min(cand[0], std::min(cand[1], cand[2]));
+      t[L.vhi + i * M + j] = std::max(cand[0], std::max(cand[1], cand[2]));
+    }
+  }
+  for (int k = 0; k < M; ++k)
+    for (int l = 0; l < M; ++l)
+      for (int b = 0; b < N; ++b)
+        for (int a = 0; a < N; ++a) {
+          const double A[2] = {t[L.vlo + a * M + k], t[L.vhi + a * M + k]};
+          const double B[2] = {t[L.vlo + b * M + l], t[L.vhi + b * M + l]};
+          double mn = A[0] * B[0], mx = mn;
+          for (int x = 0; x < 2; ++x)
+            for (int y = 0; y < 2; ++y) {
+              mn = std::min(mn, A[x] * B[y]);
+              mx = std::max(mx, A[x] * B[y]);
+            }
+          const int idx = ((k * M + l) * N + b) * N + a;
+          t[L.pmin + idx] = mn;
+          t[L.pmax + idx] = mx;
+        }
+  return t;
+}
+
+// ---- device: boxes ----------------------------------------------------------
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+constexpr int kBoxThreads = 128;
+
+// Box expansion (Sec. 3.1.1, 10% by default; Sec. 4.1 for zero extents):
+// extent L grows to (1+tol) L about the centre; an extent <= 1e-12 of the
+// largest one is padded by tol * (smallest other extent) instead.
+__device__ void expand(int d, const double* lo, const double* hi, double tol, double* mid, double* hw) {
+  double Lmax = 0.0;
+  for (int c = 0; c < d; ++c) Lmax = fmax(Lmax, hi[c] - lo[c]);
+  double Lmin = INFINITY;
+  for (int c = 0; c < d; ++c) {
+    const double L = hi[c] - lo[c];
+    if (L > 1e-12 * Lmax && L < Lmin) Lmin = L;
+  }
+  for (int c = 0; c < d; ++c) {
+    const double L = hi[c] - lo[c];
+    double pad = (L > 1e-12 * Lmax) ? 0.5 * tol * L : 0.5 * tol * Lmin;
+    if (!isfinite(pad)) pad = 0.0;
+    mid[c] = 0.5 * (lo[c] + hi[c]);
+    hw[c] = 0.5 * L + pad;
+  }
+}
+
+// One CTA per element.  AABB: bounds of each coordinate over the element's
+// boundary pieces (quad edges, hex faces) or over the element itself
+// (surface quads), Eqs. 1D_bound_final / 2D_function_bound.  OBB: the same
+// bounds of the nodes mapped by T = J_c^{-1} (volumes, Eq.
+// OBB_transformation) or T = [t1 t2 n]^{-1} (surfaces; this is the paper's
+// R2 R1 of Sec. 4.2 written as one inverse: R1 is a rotation taking n to
+// e3, and R2 R1 maps t1, t2, n to e1, e2, e3).
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kBoxThreads)
+    k_boxes(const double* __restrict__ coords, int64_t NE, const double* __restrict__ tab, int M,
+            BasisTab B, double tol, double* __restrict__ aabb, double* __restrict__ obb_c,
+            double* __restrict__ obb_A, int* status) {
+  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  constexpr int NPIECE = (DR == 3) ? 6 : (D == 2 ? 4 : 1);
+  constexpr int PIECE = (DR == 3 || D == 3) ? N * N : N;  // values per piece
+  const TabLayout L(N, M);
+  __shared__ double X[D * NN];
+  __shared__ double Xt[D * NN];
+  __shared__ double u[N * N];
+  __shared__ double lin[3];
+  __shared__ double T[9], Ti[9], xc[3];
+  __shared__ double red[2][kBoxThreads / 32];
+  __shared__ double blo[2][3], bhi[2][3];
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  for (int idx = tid; idx < D * NN; idx += blockDim.x) {
+    const int c = idx / NN, n = idx % NN;
+    X[idx] = coords[((int64_t)c * NE + e) * NN + n];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // centre x(0) and Jacobian J_c = G(0) (sum over all nodes)
+    double ph[N], dph[N];
+    lagrange<N, double>(B.z, B.w, 0.0, ph, dph);
+    double J[9];
+    for (int c = 0; c < D; ++c) {
+      double xv = 0.0, g[3] = {0.0, 0.0, 0.0};
+      for (int n = 0; n < NN; ++n) {
+        const int i = n % N, j = (n / N) % N, k = n / (N * N);
+        const double v = X[c * NN + n];
+        if (DR == 3) {
+          xv += v * ph[i] * ph[j] * ph[k];
+          g[0] += v * dph[i] * ph[j] * ph[k];
+          g[1] += v * ph[i] * dph[j] * ph[k];
+          g[2] += v * ph[i] * ph[j] * dph[k];
+        } else {
+          xv += v * ph[i] * ph[j];
+          g[0] += v * dph[i] * ph[j];
+          g[1] += v * ph[i] * dph[j];
+        }
+      }
+      xc[c] = xv;
+      for (int j = 0; j < DR; ++j) J[c * DR + j] = g[j];
+    }
+    double Mx[9];
+    if (DR == D) {
+      for (int q = 0; q < D * D; ++q) Mx[q] = J[q];
+    } else {  // [t1 t2 n/|n|] as columns
+      const double t1[3] = {J[0], J[2], J[4]}, t2[3] = {J[1], J[3], J[5]};
+      double n[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
+                     t1[0] * t2[1] - t1[1] * t2[0]};
+      const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      for (int c = 0; c < 3; ++c) {
+        Mx[c * 3 + 0] = t1[c];
+        Mx[c * 3 + 1] = t2[c];
+        Mx[c * 3 + 2] = n[c] / nn;
+      }
+    }
+    double det;
+    if (D == 2) {
+      det = Mx[0] * Mx[3] - Mx[1] * Mx[2];
+      T[0] = Mx[3] / det; T[1] = -Mx[1] / det;
+      T[2] = -Mx[2] / det; T[3] = Mx[0] / det;
+    } else {
+      const double c00 = Mx[4] * Mx[8] - Mx[5] * Mx[7];
+      const double c01 = Mx[5] * Mx[6] - Mx[3] * Mx[8];
+      const double c02 = Mx[3] * Mx[7] - Mx[4] * Mx[6];
+      det = Mx[0] * c00 + Mx[1] * c01 + Mx[2] * c02;
+      T[0] = c00 / det;
+      T[1] = (Mx[2] * Mx[7] - Mx[1] * Mx[8]) / det;
+      T[2] = (Mx[1] * Mx[5] - Mx[2] * Mx[4]) / det;
+      T[3] = c01 / det;
+      T[4] = (Mx[0] * Mx[8] - Mx[2] * Mx[6]) / det;
+      T[5] = (Mx[2] * Mx[3] - Mx[0] * Mx[5]) / det;
+      T[6] = c02 / det;
+      T[7] = (Mx[1] * Mx[6] - Mx[0] * Mx[7]) / det;
+      T[8] = (Mx[0] * Mx[4] - Mx[1] * Mx[3]) / det;
+    }
+    if (!(det != 0.0) || !isfinite(det)) record_status(status, FP_DEV_DEGENERATE);
+    for (int q = 0; q < D * D; ++q) Ti[q] = Mx[q];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < D * NN; idx += blockDim.x) {
+    const int c = idx / NN, n = idx % NN;
+    double s = 0.0;
+    for (int q = 0; q < D; ++q) s += T[c * D + q] * (X[q * NN + n] - xc[q]);
+    Xt[idx] = s;
+  }
+  __syncthreads();
+  const double* c0 = tab + L.c0;
+  const double* c1 = tab + L.c1;
+  const double* eta = tab + L.eta;
+  for (int kind = 0; kind < 2; ++kind) {
+    const double* src = kind ? Xt : X;
+    for (int c = 0; c < D; ++c) {
+      double tlo = INFINITY, thi = -INFINITY;
+      for (int piece = 0; piece < NPIECE; ++piece) {
+        // gather the piece's nodal values
+        for (int idx = tid; idx < PIECE; idx += blockDim.x) {
+          int n;
+          if (DR == 3) {
+            const int a = idx % N, b = idx / N, fixed = piece / 2;
+            const int val = (piece % 2) ? N - 1 : 0;
+            const int i = fixed == 0 ? val : a;
+            const int j = fixed == 0 ? a : (fixed == 1 ? val : b);
+            const int k = fixed == 2 ? val : b;
+            n = i + N * (j + N * k);
+          } else if (D == 3) {
+            n = idx;
+          } else {
+            const int a = idx;
+            int i, j;
+            if (piece == 0) { i = a; j = 0; }
+            else if (piece == 1) { i = a; j = N - 1; }
+            else if (piece == 2) { i = 0; j = a; }
+            else { i = N - 1; j = a; }
+            n = i + N * j;
+          }
+          u[idx] = src[c * NN + n];
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double a00 = 0.0, a10 = 0.0, a01 = 0.0;
+          if (PIECE == N) {
+            for (int a = 0; a < N; ++a) {
+              a00 += c0[a] * u[a];
+              a10 += c1[a] * u[a];
+            }
+          } else {
+            for (int b = 0; b < N; ++b)
+              for (int a = 0; a < N; ++a) {
+                const double v = u[a + N * b];
+                a00 += c0[a] * c0[b] * v;
+                a10 += c1[a] * c0[b] * v;
+                a01 += c0[a] * c1[b] * v;
+              }
+          }
+          lin[0] = a00;
+          lin[1] = a10;
+          lin[2] = a01;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < PIECE; idx += blockDim.x) {
+          const int a = idx % N, b = idx / N;
+          u[idx] -= lin[0] + lin[1] * B.z[a] + (PIECE == N ? 0.0 : lin[2] * B.z[b]);
+        }
+        __syncthreads();
+        if (PIECE == N) {
+          const double* vlo = tab + L.vlo;
+          const double* vhi = tab + L.vhi;
+          for (int j = tid; j < M; j += blockDim.x) {
+            double l = lin[0] + lin[1] * eta[j], h = l;
+            for (int a = 0; a < N; ++a) {
+              const double p = u[a] * vlo[a * M + j], q = u[a] * vhi[a * M + j];
+              l += fmin(p, q);
+              h += fmax(p, q);
+            }
+            tlo = fmin(tlo, l);
+            thi = fmax(thi, h);
+          }
+        } else {
+          const double* pmin = tab + L.pmin;
+          const double* pmax = tab + L.pmax;
+          for (int g = tid; g < M * M; g += blockDim.x) {
+            const int k = g / M, l = g % M;
+            double lo = lin[0] + lin[1] * eta[k] + lin[2] * eta[l], hi = lo;
+            const double* pn = pmin + (size_t)g * N * N;
+            const double* px = pmax + (size_t)g * N * N;
+            for (int ab = 0; ab < N * N; ++ab) {
+              const double w = u[ab];
+              const double pl = __ldg(pn + ab), ph = __ldg(px + ab);
+              lo = fma(w, w >= 0.0 ? pl : ph, lo);
+              hi = fma(w, w >= 0.0 ? ph : pl, hi);
+            }
+            tlo = fmin(tlo, lo);
+            thi = fmax(thi, hi);
+          }
+        }
+        __syncthreads();
+      }
+      tlo = warp_min(tlo);
+      thi = warp_max(thi);
+      if ((tid & 31) == 0) {
+        red[0][tid >> 5] = tlo;
+        red[1][tid >> 5] = thi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double a = red[0][0], b = red[1][0];
+        for (int w = 1; w < kBoxThreads / 32; ++w) {
+          a = fmin(a, red[0][w]);
+          b = fmax(b, red[1][w]);
+        }
+        blo[kind][c] = a;
+        bhi[kind][c] = b;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    double mid[3], hw[3];
+    expand(D, blo[0], bhi[0], tol, mid, hw);
+    for (int c = 0; c < D; ++c) {
+      aabb[e * 2 * D + c] = mid[c] - hw[c];
+      aabb[e * 2 * D + D + c] = mid[c] + hw[c];
+    }
+    expand(D, blo[1], bhi[1], tol, mid, hw);
+    for (int c = 0; c < D; ++c) {
+      double s = xc[c];
+      for (int q = 0; q < D; ++q) s += Ti[c * D + q] * mid[q];
+      obb_c[e * D + c] = s;
+      for (int q = 0; q < D; ++q) obb_A[(e * D + c) * D + q] = T[c * D + q] / hw[c];
+    }
+  }
+}
+
+// ---- device: Psi_L ------------------------------------------------------------
+
+__global__ void k_grid_bounds(const double* __restrict__ aabb, int64_t NE, int d, double* out) {
+  __shared__ double s[2][3][32];
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t e = threadIdx.x; e < NE; e += blockDim.x)
+    for (int c = 0; c < d; ++c) {
+      lo[c] = fmin(lo[c], aabb[e * 2 * d + c]);
+      hi[c] = fmax(hi[c], aabb[e * 2 * d + d + c]);
+    }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int c = 0; c < d; ++c) {
+    lo[c] = warp_min(lo[c]);
+    hi[c] = warp_max(hi[c]);
+    if (l == 0) {
+      s[0][c][w] = lo[c];
+      s[1][c][w] = hi[c];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int c = 0; c < d; ++c) {
+      double a = s[0][c][0], b = s[1][c][0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+        a = fmin(a, s[0][c][q]);
+        b = fmax(b, s[1][c][q]);
+      }
+      out[c] = a;
+      out[3 + c] = b;
+    }
+}
+
+struct GridView {
+  double lo[3], scale[3];
+  int NL, d;
+};
+
+__device__ __forceinline__ void cell_range(const GridView& g, const double* box, int* c0, int* c1) {
+  for (int c = 0; c < 3; ++c) {
+    c0[c] = 0;
+    c1[c] = 0;
+  }
+  for (int c = 0; c < g.d; ++c) {
+    c0[c] = cell_coord(box[c], g.lo[c], g.scale[c], g.NL);
+    c1[c] = cell_coord(box[g.d + c], g.lo[c], g.scale[c], g.NL);
+  }
+}
+
+// MODE 0: count entries per cell; MODE 1: place element ids.
+template <int MODE>
+__global__ void k_grid_scatter(const double* __restrict__ aabb, int64_t NE, GridView g,
+                               int* __restrict__ counter, const int* __restrict__ start,
+                               int* __restrict__ elems) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < NE;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int c0[3], c1[3];
+    cell_range(g, aabb + e * 2 * g.d, c0, c1);
+    for (int k = c0[2]; k <= c1[2]; ++k)
+      for (int j = c0[1]; j <= c1[1]; ++j)
+        for (int i = c0[0]; i <= c1[0]; ++i) {
+          const int64_t cell = i + (int64_t)g.NL * (j + (int64_t)g.NL * k);
+          const int pos = atomicAdd(&counter[cell], 1);
+          if (MODE == 1) elems[start[cell] + pos] = (int)e;
+        }
+  }
+}
+
+// Exclusive scan of counts[0..n) into start[0..n], start[n] = total, by one
+// CTA: each thread scans a contiguous chunk.
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ counts, int64_t n,
+                                               int* __restrict__ start) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x;
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t b = t * chunk, en = b + chunk < n ? b + chunk : n;
+  long long s = 0;
+  for (int64_t i = b; i < en; ++i) s += counts[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    long long v = (t >= o) ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  long long run = part[t] - s;
+  for (int64_t i = b; i < en; ++i) {
+    start[i] = (int)run;
+    run += counts[i];
+  }
+  if (t == (int)blockDim.x - 1) start[n] = (int)part[t];
+}
+
+// Ascending element ids within each cell (insertion sort; lists are short).
+__global__ void k_grid_sort(const int* __restrict__ start, int64_t ncell, int* __restrict__ elems) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int b = start[c], en = start[c + 1];
+    for (int i = b + 1; i < en; ++i) {
+      const int v = elems[i];
+      int j = i - 1;
+      while (j >= b && elems[j] > v) {
+        elems[j + 1] = elems[j];
+        --j;
+      }
+      elems[j + 1] = v;
+    }
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t count, size_t* bytes) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return FP_ENOMEM;
+  }
+  *bytes += count * sizeof(T);
+  return FP_OK;
+}
+
+void free_mesh_memory(fp_mesh_s* m) {
+  cudaFree(m->coords);
+  cudaFree(m->coords32);
+  cudaFree(m->aabb);
+  cudaFree(m->obb_c);
+  cudaFree(m->obb_A);
+  cudaFree(m->box32);
+  cudaFree(m->cell_start);
+  cudaFree(m->cell_elems);
+  cudaFree(m->status);
+}
+
+int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st);
+
+}  // namespace
+}  // namespace fp
+
+int fp_mixed_prepare(fp_mesh_s* m, cudaStream_t st);  // find.cu
+
+fp::DevMesh fp_mesh_s::view() const {
+  fp::DevMesh v;
+  v.coords = coords;
+  v.coords32 = coords32;
+  v.aabb = aabb;
+  v.obb_c = obb_c;
+  v.obb_A = obb_A;
+  v.box32 = box32;
+  v.cell_start = cell_start;
+  v.cell_elems = cell_elems;
+  v.NE = NE;
+  v.cstride = NE * (int64_t)ne;
+  for (int c = 0; c < 3; ++c) {
+    v.lo[c] = lo[c];
+    v.hi[c] = hi[c];
+    v.scale[c] = scale[c];
+  }
+  v.NL = NL;
+  v.max_iter = opts.max_iter;
+  v.newton_tol = opts.newton_tol;
+  v.dist_tol = opts.dist_tol;
+  v.status = status;
+  return v;
+}
+
+namespace fp {
+namespace {
+
+int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
+  // element boxes
+  const std::vector<double> htab = bound_tables(m->N, m->M);
+  double* dtab = nullptr;
+  FP_CUDA_TRY(cudaMalloc(&dtab, htab.size() * sizeof(double)));
+  int rc = FP_OK;
+  do {
+    if (cudaMemcpyAsync(dtab, htab.data(), htab.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+    rc = dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+      constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
+      k_boxes<N, D, DR><<<(unsigned)m->NE, kBoxThreads, 0, st>>>(
+          m->coords, m->NE, dtab, m->M, m->basis, m->opts.bbox_tol, m->aabb, m->obb_c, m->obb_A,
+          m->status);
+      return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+    });
+    if (rc != FP_OK) break;
+    // grid bounds = union of the expanded AABBs
+    double* dbounds = nullptr;
+    if (cudaMalloc(&dbounds, 6 * sizeof(double)) != cudaSuccess) {
+      rc = FP_ENOMEM;
+      break;
+    }
+    k_grid_bounds<<<1, 1024, 0, st>>>(m->aabb, m->NE, m->d, dbounds);
+    double hb[6];
+    cudaError_t ce = cudaMemcpyAsync(hb, dbounds, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    cudaFree(dbounds);
+    if (ce != cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+    int NL = m->opts.n_grid;
+    if (NL <= 0) {
+      NL = 1;
+      while (true) {
+        int64_t p = 1;
+        for (int c = 0; c < m->d; ++c) p *= NL;
+        if (p >= m->NE) break;
+        ++NL;
+      }
+    }
+    int64_t ncell = 1;
+    for (int c = 0; c < m->d; ++c) ncell *= NL;
+    if (ncell > (int64_t)1 << 28) {
+      rc = FP_EINVAL;
+      break;
+    }
+    m->NL = NL;
+    m->ncell = ncell;
+    GridView g;
+    g.NL = NL;
+    g.d = m->d;
+    for (int c = 0; c < 3; ++c) {
+      m->lo[c] = (c < m->d) ? hb[c] : 0.0;
+      m->hi[c] = (c < m->d) ? hb[3 + c] : 0.0;
+      const double ext = m->hi[c] - m->lo[c];
+      m->scale[c] = (c < m->d && ext > 0.0) ? (double)NL / ext : 0.0;
+      g.lo[c] = m->lo[c];
+      g.scale[c] = m->scale[c];
+    }
+    int* counts = nullptr;
+    if ((rc = dev_alloc(&m->cell_start, ncell + 1, &m->bytes)) != FP_OK) break;
+    if (cudaMalloc(&counts, ncell * sizeof(int)) != cudaSuccess) {
+      rc = FP_ENOMEM;
+      break;
+    }
+    const int eb = grid_for(m->NE, 256, 148 * 16);
+    cudaMemsetAsync(counts, 0, ncell * sizeof(int), st);
+    k_grid_scatter<0><<<eb, 256, 0, st>>>(m->aabb, m->NE, g, counts, nullptr, nullptr);
+    k_scan<<<1, 1024, 0, st>>>(counts, ncell, m->cell_start);
+    int nnz = 0;
+    ce = cudaMemcpyAsync(&nnz, m->cell_start + ncell, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess || nnz < 0) {
+      cudaFree(counts);
+      rc = ce != cudaSuccess ? FP_ELAUNCH : FP_ENOMEM;
+      break;
+    }
+    m->nnz = nnz;
+    if ((rc = dev_alloc(&m->cell_elems, (size_t)nnz, &m->bytes)) != FP_OK) {
+      cudaFree(counts);
+      break;
+    }
+    cudaMemsetAsync(counts, 0, ncell * sizeof(int), st);
+    k_grid_scatter<1><<<eb, 256, 0, st>>>(m->aabb, m->NE, g, counts, m->cell_start, m->cell_elems);
+    k_grid_sort<<<grid_for(ncell, 256, 148 * 16), 256, 0, st>>>(m->cell_start, ncell, m->cell_elems);
+    ce = cudaStreamSynchronize(st);
+    cudaFree(counts);
+    if (ce != cudaSuccess) rc = FP_ELAUNCH;
+  } while (0);
+  cudaFree(dtab);
+  return rc;
+}
+
+}  // namespace
+}  // namespace fp
+
+extern "C" void fp_opts_default(fp_opts* o) {
+  if (!o) return;
+  o->bbox_tol = 0.1;
+  o->M = 0;
+  o->n_grid = 0;
+  o->newton_tol = 1e-10;
+  o->max_iter = 50;
+  o->dist_tol = 1e-10;
+  o->precision = FP_F64;
+}
+
+extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int64_t NE,
+                        const fp_opts* opts, void* stream, fp_mesh* out) {
+  using namespace fp;
+  if (!out) return FP_EINVAL;
+  *out = nullptr;
+  if (!coords_dev || NE <= 0 || NE > INT32_MAX) return FP_EINVAL;
+  if (!((d == 2 && dr == 2) || (d == 3 && dr == 3) || (d == 3 && dr == 2))) return FP_EINVAL;
+  const int N = order + 1;
+  if (order < 1) return FP_EINVAL;
+  if (N > FP_MAX_N) return FP_EUNSUPPORTED;
+  fp_opts o;
+  fp_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.M == 0) o.M = 2 * N;
+  if (o.M < 2 || o.M > kMaxM || !(o.bbox_tol >= 0.0) || o.max_iter < 1 || !(o.newton_tol > 0.0) ||
+      o.n_grid < 0 || (o.precision != FP_F64 && o.precision != FP_MIXED))
+    return FP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  fp_mesh_s* m = (fp_mesh_s*)calloc(1, sizeof(fp_mesh_s));
+  if (!m) return FP_ENOMEM;
+  m->d = d;
+  m->dr = dr;
+  m->N = N;
+  m->ne = (dr == 3) ? N * N * N : N * N;
+  m->M = o.M;
+  m->NE = NE;
+  m->opts = o;
+  m->precision = o.precision;
+  host_basis_tab(N, &m->basis);
+  const size_t nc = (size_t)d * NE * m->ne;
+  int rc = FP_OK;
+  do {
+    if ((rc = dev_alloc(&m->coords, nc, &m->bytes)) != FP_OK) break;
+    if ((rc = dev_alloc(&m->coords32, nc, &m->bytes)) != FP_OK) break;
+    if ((rc = dev_alloc(&m->aabb, (size_t)NE * 2 * d, &m->bytes)) != FP_OK) break;
+    if ((rc = dev_alloc(&m->obb_c, (size_t)NE * d, &m->bytes)) != FP_OK) break;
+    if ((rc = dev_alloc(&m->obb_A, (size_t)NE * d * d, &m->bytes)) != FP_OK) break;
+    if ((rc = dev_alloc(&m->status, 1, &m->bytes)) != FP_OK) break;
+    if (cudaMemsetAsync(m->status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemcpyAsync(m->coords, coords_dev, nc * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+    k_to_float<<<grid_for((int64_t)nc, 256, 148 * 16), 256, 0, st>>>(m->coords, (int64_t)nc, m->coords32);
+    if ((rc = build_boxes_and_grid(m, st)) != FP_OK) break;
+    if ((rc = fp_mixed_prepare(m, st)) != FP_OK) break;
+    int hstat = 0;
+    if (cudaMemcpyAsync(&hstat, m->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+    if (hstat != 0) rc = FP_EINVAL;  // a degenerate element (singular J at its centre)
+  } while (0);
+  if (rc != FP_OK) {
+    cudaStreamSynchronize(st);
+    free_mesh_memory(m);
+    free(m);
+    return rc;
+  }
+  *out = m;
+  return FP_OK;
+}
+
+extern "C" int fp_free(fp_mesh m) {
+  if (!m) return FP_EINVAL;
+  cudaDeviceSynchronize();
+  fp::free_mesh_memory(m);
+  free(m);
+  return FP_OK;
+}
+
+extern "C" int fp_get_info(fp_mesh m, fp_mesh_info* info) {
+  if (!m || !info) return FP_EINVAL;
+  memset(info, 0, sizeof(*info));
+  info->d = m->d;
+  info->dr = m->dr;
+  info->N = m->N;
+  info->M = m->M;
+  info->n_grid = m->NL;
+  info->NE = m->NE;
+  info->n_cells = m->ncell;
+  info->n_cell_entries = m->nnz;
+  for (int c = 0; c < 3; ++c) {
+    info->grid_lo[c] = m->lo[c];
+    info->grid_hi[c] = m->hi[c];
+  }
+  info->device_bytes = m->bytes;
+  return FP_OK;
+}
+
+extern "C" int fp_get_boxes(fp_mesh m, double* aabb, double* obb_c, double* obb_A, void* stream) {
+  if (!m) return FP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t d = m->d;
+  if (aabb) FP_CUDA_TRY(cudaMemcpyAsync(aabb, m->aabb, m->NE * 2 * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (obb_c) FP_CUDA_TRY(cudaMemcpyAsync(obb_c, m->obb_c, m->NE * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (obb_A) FP_CUDA_TRY(cudaMemcpyAsync(obb_A, m->obb_A, m->NE * d * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  FP_CUDA_TRY(cudaStreamSynchronize(st));
+  return FP_OK;
+}
+
+extern "C" int fp_get_grid(fp_mesh m, int32_t* cell_start, int32_t* cell_elems, void* stream) {
+  if (!m) return FP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cell_start)
+    FP_CUDA_TRY(cudaMemcpyAsync(cell_start, m->cell_start, (m->ncell + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  if (cell_elems && m->nnz > 0)
+    FP_CUDA_TRY(cudaMemcpyAsync(cell_elems, m->cell_elems, m->nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  FP_CUDA_TRY(cudaStreamSynchronize(st));
+  return FP_OK;
+}
+
+extern "C" int fp_device_status(fp_mesh m, int* status, void* stream) {
+  if (!m || !status) return FP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  FP_CUDA_TRY(cudaMemcpyAsync(status, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FP_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));
+  FP_CUDA_TRY(cudaStreamSynchronize(st));
+  return FP_OK;
+}
+
+extern "C" const char* fp_status_string(int s) {
+  switch (s) {
+    case FP_OK: return "ok";
+    case FP_EINVAL: return "invalid argument";
+    case FP_ENOMEM: return "out of device memory or over budget";
+    case FP_ELAUNCH: return "kernel launch or CUDA runtime failure";
+    case FP_EDEVICE: return "a kernel recorded a device error";
+    case FP_ETIMEDOUT: return "timed out";
+    case FP_EBUSY: return "busy";
+    case FP_EUNSUPPORTED: return "element type or order not supported";
+    default: return "unknown status";
+  }
+}

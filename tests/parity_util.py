@@ -1,0 +1,52 @@
+"""Shared comparison of GPU results with the FP64 oracle.
+
+Tolerances (FP64 path): element id and code identical; r within 1e-10;
+dist2 within 1e-12 relative + 1e-24 absolute; interpolated values within
+1e-12 relative to max(|oracle value|, max |nodal value| of the element).
+
+Where several answers are correct the comparison checks what is unique: a
+BORDER point whose closest boundary point is shared by two candidate
+elements has two valid element ids with equal dist2, so a differing
+BORDER element is accepted only when both dist2 values agree to 1e-12.
+"""
+import numpy as np
+
+R_TOL = 1e-10
+D2_REL, D2_ABS = 1e-12, 1e-24
+U_REL = 1e-12
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label=""):
+    oc, oe, orr, od = oracle_out
+    gc, ge, gr, gd = gpu_out
+    mism = (oc != gc) | (oe != ge)
+    tie = mism & (oc == 1) & (gc == 1) & (np.abs(od - gd) <= D2_REL * np.abs(od) + D2_ABS)
+    bad = np.flatnonzero(mism & ~tie)
+    assert bad.size == 0, (
+        f"{label}: {bad.size} code/elem mismatches, e.g. idx {bad[:5]}: oracle "
+        f"{list(zip(oc[bad[:5]], oe[bad[:5]]))} gpu {list(zip(gc[bad[:5]], ge[bad[:5]]))}")
+    same = ~mism & (oc != 2)
+    if same.any():
+        dr = np.max(np.abs(orr[same] - gr[same]))
+        assert dr <= r_tol, f"{label}: max |dr| = {dr:.3e}"
+        dd = np.abs(od[same] - gd[same]) - (D2_REL * np.abs(od[same]) + D2_ABS)
+        assert np.max(dd) <= 0, f"{label}: dist2 mismatch {np.max(dd):.3e}"
+    nf = oc == 2
+    assert np.all(ge[nf] == -1) and np.all(np.isinf(gd[nf])) and np.all(gr[nf] == 0)
+    return {"n": len(oc), "ties": int(tie.sum()), "codes": np.bincount(gc, minlength=3).tolist()}
+
+
+def compare_eval(field, NE, ne, elem, u_oracle, u_gpu, label=""):
+    """u arrays [nc][n]; scale per point = max(|u_oracle|, max nodal |u| in e)."""
+    nc = u_oracle.shape[0]
+    f = field.reshape(nc, NE, ne)
+    e = np.where(elem >= 0, elem, 0)
+    nodal = np.abs(f[:, e, :]).max(axis=2)  # [nc][n]
+    scale = np.maximum(np.abs(u_oracle), nodal)
+    err = np.abs(u_oracle - u_gpu) - U_REL * scale
+    assert np.max(err) <= 0, f"{label}: eval mismatch, worst excess {np.max(err):.3e}"
+    assert np.all(u_gpu[:, elem < 0] == 0.0)

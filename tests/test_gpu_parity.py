@@ -1,0 +1,228 @@
+"""GPU (CUDA path, through the C ABI) against the FP64 oracle: boxes, Psi_L,
+find and eval on every element shape and order, small cases in full and
+the full-size 3D workload on a seeded sample."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_12349_b300 import workloads as W
+from parity_util import compare_eval, compare_find, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+@pytest.fixture(scope="module")
+def fp():
+    import paper_2501_12349_b300 as f
+    f.lib()
+    return f
+
+
+def gpu_mesh(fp, torch, coords, d, dr, order, **opts):
+    return fp.Mesh(torch.from_numpy(np.ascontiguousarray(coords)).cuda(), d, dr, order, **opts)
+
+
+def gpu_find(torch, mesh, pts):
+    out = mesh.find(torch.from_numpy(np.ascontiguousarray(pts)).cuda())
+    return tuple(to_np(t) for t in out)
+
+
+def surface_points(om, rng, n, h, frac_off=0.1):
+    elem = rng.integers(0, om.NE, n).astype(np.int32)
+    rt = rng.uniform(-1.0, 1.0, (n, 2))
+    x, J = om.forward_map(elem, rt, jacobian=True)
+    nrm = np.cross(J[:, :, 0], J[:, :, 1])
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    off = rng.uniform(size=n) < frac_off
+    x[off] += 0.01 * h * nrm[off]
+    return x
+
+
+CASES = {
+    "quad2d_p3": lambda: (W.config1().coords, 2, 2, 3, 1.0 / 8),
+    "hex3d_p4": lambda: (W.hex_mesh(6, 4, 0.3), 3, 3, 4, 1.0 / 6),
+    "sphere_p4": lambda: (W.cubed_sphere(3, 4), 3, 2, 4, np.pi / 6),
+    "torus_p3": lambda: (W.torus(12, 4, 3), 3, 2, 3, 2 * np.pi * 0.3 / 4),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_boxes_and_grid(fp, torch, case):
+    coords, d, dr, order, h = CASES[case]()
+    N = order + 1
+    om = oracle.OracleMesh(coords, d, dr, N)
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    aabb, oc, oA = (to_np(t) for t in m.boxes())
+    scale = np.abs(om.aabb).max(axis=1, keepdims=True)
+    assert np.max(np.abs(aabb - om.aabb) / scale) < 1e-12
+    assert np.max(np.abs(oc - om.obb_c) / scale) < 1e-12
+    Ascale = np.abs(om.obb_A).reshape(om.NE, -1).max(axis=1)[:, None, None]
+    assert np.max(np.abs(oA - om.obb_A) / Ascale) < 1e-12
+    # Psi_L: recomputed from the GPU's own boxes with the same rounded
+    # formulas, it must match the GPU's CSR exactly (integer work).
+    info = m.info()
+    NL = info.n_grid
+    assert NL ** d >= om.NE and (NL - 1) ** d < om.NE
+    lo = np.array(info.grid_lo[:d])
+    hi = np.array(info.grid_hi[:d])
+    np.testing.assert_array_equal(lo, aabb[:, :d].min(0))
+    np.testing.assert_array_equal(hi, aabb[:, d:].max(0))
+    sc = np.where(hi > lo, NL / np.where(hi > lo, hi - lo, 1.0), 0.0)
+
+    def cell(x, c):
+        t = (x - lo[c]) * sc[c]
+        return np.clip(np.where(t >= NL, NL - 1, np.floor(t)), 0, NL - 1).astype(np.int64)
+
+    lists = [[] for _ in range(NL ** d)]
+    for e in range(om.NE):
+        c0 = [cell(aabb[e, c], c) for c in range(d)]
+        c1 = [cell(aabb[e, d + c], c) for c in range(d)]
+        rng3 = [range(c0[c], c1[c] + 1) for c in range(d)]
+        if d == 2:
+            for j in rng3[1]:
+                for i in rng3[0]:
+                    lists[i + NL * j].append(e)
+        else:
+            for k in rng3[2]:
+                for j in rng3[1]:
+                    for i in rng3[0]:
+                        lists[i + NL * (j + NL * k)].append(e)
+    cs, ce = (to_np(t) for t in m.grid())
+    exp_start = np.concatenate([[0], np.cumsum([len(l) for l in lists])])
+    np.testing.assert_array_equal(cs, exp_start)
+    np.testing.assert_array_equal(ce, np.concatenate([np.array(l, np.int32) for l in lists]))
+    assert m.device_status() == 0
+    m.close()
+
+
+def test_find_eval_config1_full(fp, torch):
+    w = W.config1()
+    om = oracle.OracleMesh(w.coords, 2, 2, w.N)
+    pts = np.concatenate([om.forward_map(w.fwd_elem, w.fwd_r), w.pts])
+    m = gpu_mesh(fp, torch, w.coords, 2, 2, w.order)
+    g = gpu_find(torch, m, pts)
+    o = om.findpts(pts)
+    compare_find(o, g, label="config1")
+    assert np.array_equal(g[1][:len(w.fwd_elem)], w.fwd_elem)
+    assert np.max(np.abs(g[2][:len(w.fwd_elem)] - w.fwd_r)) < 1e-10
+    code, elem, r = (torch.from_numpy(a).cuda() for a in g[:3])
+    u = to_np(m.eval(code, elem, r, torch.from_numpy(w.field).cuda()))
+    compare_eval(w.field, om.NE, w.N ** 2, o[1], om.eval(w.field, *o[:3]), u, "config1 eval")
+    m.close()
+
+
+@pytest.mark.parametrize("case", ["hex3d_p4", "sphere_p4", "torus_p3"])
+def test_find_eval_small_full(fp, torch, case):
+    coords, d, dr, order, h = CASES[case]()
+    N = order + 1
+    om = oracle.OracleMesh(coords, d, dr, N)
+    rng = np.random.default_rng(11)
+    if dr == 3:
+        pts = rng.uniform(-0.02, 1.02, (20000, 3))
+    else:
+        pts = surface_points(om, rng, 20000, h)
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    g = gpu_find(torch, m, pts)
+    o = om.findpts(pts)
+    res = compare_find(o, g, label=case)
+    assert res["codes"][0] > 0
+    fld, _ = W.polynomial_field(coords, rng, order, nc=3)
+    code, elem, r = (torch.from_numpy(a).cuda() for a in g[:3])
+    u = to_np(m.eval(code, elem, r, torch.from_numpy(fld).cuda()))
+    compare_eval(fld, om.NE, N ** dr, o[1], om.eval(fld, *o[:3]), u, case + " eval")
+    # coordinate-field invariant on the GPU alone: |u_x - x*|^2 = dist2
+    ux = to_np(m.eval(code, elem, r, torch.from_numpy(coords).cuda()))
+    found = g[0] != 2
+    err = np.sum((ux[:, found].T - pts[found]) ** 2, axis=1)
+    np.testing.assert_allclose(err, g[3][found], rtol=1e-9, atol=1e-22)
+    assert m.device_status() == 0
+    m.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("shape", ["quad2d", "hex3d"])
+def test_every_order(fp, torch, shape, order):
+    rng = np.random.default_rng(100 + order)
+    if shape == "quad2d":
+        coords, d, dr = W.quad_mesh(5, order, amp=0.2, kind="kershaw"), 2, 2
+    else:
+        coords, d, dr = W.hex_mesh(3, order, 0.25), 3, 3
+    om = oracle.OracleMesh(coords, d, dr, order + 1)
+    pts = rng.uniform(-0.05, 1.05, (3000, d))
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    compare_find(om.findpts(pts), gpu_find(torch, m, pts), label=f"{shape} p{order}")
+    m.close()
+
+
+def test_config2_full_size_sampled(fp, torch):
+    """The full 32^3, p=4 workload (10^6 points) in one launch, as the
+    benchmark runs it; the oracle checks a seeded sample of 20,000 outputs,
+    and properties that hold at any size check the rest."""
+    w = W.config2()
+    m = gpu_mesh(fp, torch, w.coords, 3, 3, w.order)
+    pts_t = torch.from_numpy(w.pts).cuda()
+    code, elem, r, dist2 = m.find(pts_t)
+    u = m.eval(code, elem, r, torch.from_numpy(w.field).cuda())
+    g = tuple(to_np(t) for t in (code, elem, r, dist2))
+    idx = np.sort(np.random.default_rng(12).choice(len(w.pts), 20000, replace=False))
+    om = oracle.OracleMesh(w.coords, 3, 3, w.N)
+    o = om.findpts(w.pts[idx])
+    compare_find(o, tuple(a[idx] for a in g), label="config2 sample")
+    compare_eval(w.field, om.NE, w.N ** 3, o[1], om.eval(w.field, *o[:3]), to_np(u)[:, idx], "config2 eval")
+    # every point: points inside the unit cube are INTERIOR (the mesh covers
+    # it exactly), dist2 of INTERIOR points ~ 0, NOT_FOUND only outside
+    inside = np.all((w.pts > 1e-9) & (w.pts < 1 - 1e-9), axis=1)
+    assert np.all(g[0][inside] == 0)
+    assert np.all(g[3][g[0] == 0] < 1e-20)
+    assert np.all(np.abs(g[2][g[0] != 2]) <= 1.0)
+    assert np.all(~inside[g[0] == 2])
+    assert m.device_status() == 0
+    m.close()
+
+
+def test_edge_cases(fp, torch):
+    w = W.config1()
+    m = gpu_mesh(fp, torch, w.coords, 2, 2, w.order)
+    info = m.info()
+    # n == 0 is a no-op
+    e = torch.empty((0, 2), dtype=torch.float64, device="cuda")
+    c, el, r, d2 = m.find(e)
+    assert c.numel() == 0
+    # non-finite points, points beyond the grid bounds, huge values, and
+    # points clearly inside / outside the domain (points exactly on element
+    # faces or box faces are left out: rounding of equal-valued quantities
+    # decides them, and several answers are correct there)
+    hi = info.grid_hi
+    pts = np.array([[np.nan, 0.5], [0.5, np.inf], [-np.inf, 0.2], [hi[0] + 1e-9, 0.5],
+                    [1e300, -1e300], [0.3, 0.7], [-0.05, 0.5], [1.05, 1.05]])
+    om = oracle.OracleMesh(w.coords, 2, 2, w.N)
+    g = gpu_find(torch, m, pts)
+    compare_find(om.findpts(pts), g, label="edge")
+    assert np.all(g[0][:5] == 2) and g[0][5] == 0 and np.all(g[0][6:] != 0)
+    # a ragged size that is not a multiple of any block size
+    rng = np.random.default_rng(3)
+    p2 = rng.uniform(-0.2, 1.2, (1237, 2))
+    compare_find(om.findpts(p2), gpu_find(torch, m, p2), label="ragged")
+    assert m.device_status() == 0
+    m.close()
+
+
+def test_stats_counters(fp, torch):
+    w = W.hex_config(13, 5000, 1, n=6)
+    om = oracle.OracleMesh(w.coords, 3, 3, w.N)
+    m = gpu_mesh(fp, torch, w.coords, 3, 3, w.order)
+    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    m.find(torch.from_numpy(w.pts).cuda(), stats=st)
+    gs = to_np(st)
+    os_ = np.zeros(8, np.int64)
+    om.findpts(w.pts, stats=os_)
+    assert gs[0] == os_[0]                       # candidates: exact
+    assert abs(gs[1] - os_[1]) <= 0.01 * os_[1]  # iterations: same algorithm
+    m.close()
