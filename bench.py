@@ -157,6 +157,67 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist):
+    """The 10^7-point, 3-component workload on the same mesh, find + eval,
+    timed with the FP64 path and with the mixed path (FP32 filter and early
+    Newton, FP64 final steps); both results are checked against each other."""
+    w = W.config3(seed=3 + rank)
+    coords = torch.from_numpy(w.coords).to(dev)
+    field = torch.from_numpy(w.field).to(dev)
+    pts = torch.from_numpy(w.pts).to(dev)
+    n = pts.shape[0]
+    mesh = fp.Mesh(coords, 3, 3, w.order)
+    outs = {}
+    res = {"workload": "hex3d_32^3_p4_kershaw0.3_1e7pts_nc3"}
+    steps = max(3, args.steps // 2)
+    for prec in ("f64", "mixed"):
+        mesh.set_precision(fp.FP_MIXED if prec == "mixed" else fp.FP_F64)
+        code = torch.empty(n, dtype=torch.int32, device=dev)
+        elem = torch.empty(n, dtype=torch.int32, device=dev)
+        r = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        d2 = torch.empty(n, dtype=torch.float64, device=dev)
+        out = torch.empty((3, n), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            flush.zero_()
+            fp.fp_findpts(mesh.handle, pts, code, elem, r, d2)
+            fp.fp_eval(mesh.handle, code, elem, r, field, 3, out)
+        fms, ems = [], []
+        for _ in range(steps):
+            flush.zero_()
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(st)
+            fp.fp_findpts(mesh.handle, pts, code, elem, r, d2)
+            b.record(st)
+            fp.fp_eval(mesh.handle, code, elem, r, field, 3, out)
+            c.record(st)
+            c.synchronize()
+            fms.append(a.elapsed_time(b))
+            ems.append(b.elapsed_time(c))
+        t = (sum(fms) + sum(ems)) / 1e3
+        if world > 1:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        stats = torch.zeros(fp.FP_NSTATS, dtype=torch.int64, device=dev)
+        fp.fp_findpts_stats(mesh.handle, pts, code, elem, r, d2, stats)
+        sv = stats.cpu().numpy()
+        outs[prec] = (code.clone(), elem.clone(), r.clone())
+        res[prec] = {"value": world * n * steps / t, "unit": "points/s",
+                     "find_ms": statistics.mean(fms), "eval_ms": statistics.mean(ems),
+                     "counters": {"candidates": int(sv[0]), "iterations": int(sv[1]),
+                                  "fp64_refine_evals": int(sv[4]), "fp64_box_tests": int(sv[5]),
+                                  "to_fp64_kernel": int(sv[6])}}
+    a, b = outs["f64"], outs["mixed"]
+    same = (a[0] == b[0]) & (a[1] == b[1])
+    res["code_elem_mismatch_vs_f64"] = int((~same).sum().item())
+    found = same & (a[0] != 2)
+    res["max_abs_dr_vs_f64"] = float((a[2] - b[2]).abs().max(dim=1).values[found].max().item())
+    res["speedup_vs_f64"] = res["mixed"]["value"] / res["f64"]["value"]
+    res["status"] = mesh.device_status()
+    mesh.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -165,6 +226,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-mixed", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -285,6 +347,8 @@ def main():
         e2e_t = float(tt.item())
     e2e_v = world * n * args.steps / e2e_t
     status = mesh.device_status()
+    mesh.close()
+    mixed = None if args.skip_mixed else mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -309,10 +373,9 @@ def main():
                               "beta_iterations": int(sv[3]), "per_point_iterations": float(sv[1]) / n},
             "setup_ms": setup_ms, "wall_s_timed": wall, "device_status": status,
             "e2e": {"value": e2e_v, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "cpu_baseline": cpu, "clocks": clk,
+            "cpu_baseline": cpu, "clocks": clk, "mixed": mixed,
         }
         print(json.dumps(line), flush=True)
-    mesh.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -114,7 +114,9 @@ int fp_findpts(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
  * FP_NSTATS uint64 values, caller-zeroed):
  *   [0] candidates that passed the box filter  [1] Newton iterations
  *   [2] rejected trust-region steps            [3] iterations with beta = 1
- *   [4] FP64 iterations of the mixed path      [5] candidates rechecked in FP64 */
+ *   [4] FP64 refinement evaluations (mixed)    [5] box tests decided in FP64
+ *   [6] points the mixed path handed to its FP64 kernel
+ * (with FP_MIXED, [1]-[3] count FP32 and FP64 iterations together). */
 #define FP_NSTATS 8
 int fp_findpts_stats(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
                      int32_t* elem, double* r, double* dist2, uint64_t* stats_dev,

@@ -1,0 +1,465 @@
+// Pieces of the find kernels (Sec. 3.2) shared by the FP64 and mixed paths:
+// certified FP32 prefilters with exact FP64 fallbacks, the trust-region
+// Newton step of Sec. 3.2.1 split into its parts, result writes, counters.
+#pragma once
+#include <math.h>
+
+#include "fp_basis.cuh"
+#include "fp_common.cuh"
+
+namespace fp {
+
+constexpr int kFindThreads = 128;
+
+// Per-thread counters: [0] candidates, [1] Newton iterations, [2] rejected
+// steps, [3] beta = 1 iterations, [4] FP64 refinement evaluations (mixed),
+// [5] box tests decided in FP64, [6] points handed to the FP64 kernel (mixed).
+struct Counters {
+  unsigned v[7];
+  __device__ Counters() {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) v[i] = 0;
+  }
+  __device__ void flush(unsigned long long* stats) {
+    if (!stats) return;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      unsigned x = v[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) == 0 && x) atomicAdd(stats + i, (unsigned long long)x);
+    }
+  }
+};
+
+inline int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
+}
+
+// Persistent grid: per_sm CTAs per SM, fewer when n is small.
+inline int persistent_blocks(int64_t n, int per_sm) {
+  const int64_t want = (n + kFindThreads - 1) / kFindThreads;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+// ---- exact FP64 tests ---------------------------------------------------------
+
+// Eq. AABB_test (as lo <= x <= hi) and Eq. OBB_test on the expanded boxes,
+// with the same rounded operations as the FP64 definition.
+template <int D>
+__device__ __forceinline__ bool in_boxes_f64(const DevMesh& m, int64_t e, const double (&xs)[D]) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const double lo = __ldg(m.aabb + e * 2 * D + c), hi = __ldg(m.aabb + e * 2 * D + D + c);
+    if (!(xs[c] >= lo && xs[c] <= hi)) return false;
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+      s = __dadd_rn(s, __dmul_rn(__ldg(m.obb_A + (e * D + c) * D + q),
+                                 __dsub_rn(xs[q], __ldg(m.obb_c + e * D + q))));
+    if (!(fabs(s) <= 1.0)) return false;
+  }
+  return true;
+}
+
+// ---- certified FP32 tests -----------------------------------------------------
+
+// The box test of element rec in FP32: 0 = outside, 1 = inside, 2 = too
+// close to a face to decide in FP32.  The margins bound the rounding of the
+// FP32 inputs and operations (u = 2^-24): an AABB difference is off by at
+// most 2u(|x| + |b|) + u|x - b| < 4u(|x| + |b|); an OBB coordinate
+// sum_k A_jk (x_k - c_k) by at most 6u sum_k |A_jk| (|x_k| + |c_k|); the FP64
+// computation of the same quantities is off by ~1e-16 of them.  Margins of
+// 4u and 16u are used, so a decision taken here equals the FP64 one.
+template <int D>
+__device__ __forceinline__ int boxes_f32(const float* __restrict__ rec, const float (&x)[D]) {
+  int res = 1;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const float lo = __ldg(rec + c), hi = __ldg(rec + 3 + c);
+    const float dl = x[c] - lo, dh = hi - x[c];
+    const float ml = 2.3841858e-07f * (fabsf(x[c]) + fabsf(lo));  // 4u
+    const float mh = 2.3841858e-07f * (fabsf(x[c]) + fabsf(hi));
+    if (dl < -ml || dh < -mh) return 0;
+    if (!(dl > ml && dh > mh)) res = 2;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    float v = 0.f, eb = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float a = __ldg(rec + 9 + j * 3 + k), cc = __ldg(rec + 6 + k);
+      v = fmaf(a, x[k] - cc, v);
+      eb = fmaf(fabsf(a), fabsf(x[k]) + fabsf(cc), eb);
+    }
+    eb *= 9.5367432e-07f;  // 16u
+    const float av = fabsf(v);
+    if (av > 1.f + eb) return 0;
+    if (!(av < 1.f - eb)) res = 2;
+  }
+  return res;
+}
+
+// Next element of the cell list [q, qend) that passes the box filter, or -1.
+template <int D>
+__device__ __forceinline__ int next_candidate(const DevMesh& m, const double (&xs)[D],
+                                              const float (&x32)[D], int& q, int qend,
+                                              Counters& cnt) {
+  while (q < qend) {
+    const int c = __ldg(m.cell_elems + q);
+    ++q;
+    if (c < 0 || c >= m.NE) {
+      record_status(m.status, FP_DEV_BAD_ELEM);
+      continue;
+    }
+    int t = boxes_f32<D>(m.box32 + (int64_t)c * BOX32, x32);
+    if (t == 2) {
+      ++cnt.v[5];
+      t = in_boxes_f64<D>(m, c, xs) ? 1 : 0;
+    }
+    if (t == 1) return c;
+  }
+  return -1;
+}
+
+// x* relative to the element reference point, in FP64 and rounded to FP32.
+template <int D>
+__device__ __forceinline__ void rel_point(const DevMesh& m, int64_t e, const double (&xs)[D],
+                                          float (&xr)[D]) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) xr[c] = (float)(xs[c] - elem_ref(m.aabb, D, e, c));
+}
+
+// Closest GLL node of element e to xs (Sec. 3.2.1, initial guess), ties to
+// the lowest node index, as the FP64 definition computes it: squared
+// distances sum_c (x_c - X_c)^2 in non-contracted FP64.  The FP32 scan over
+// the relative coordinates (xr = fl(x* - x_ref), X32 = fl(X - x_ref)) is
+// certified when its best distance beats the second best by more than both
+// rounding bounds; otherwise the FP64 scan decides.  Bound, with
+// E = 4u (|xr|_inf + Xrel) per component (u = 2^-24, Xrel >= |X - x_ref|):
+// |d32 - d| <= 2 sqrt(D d) E + D E^2 + 8u d.
+template <int N, int D, int DR>
+__device__ int closest_node(const DevMesh& m, int e, const double (&xs)[D], const float (&xr)[D]) {
+  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  const float* X32 = m.coords32 + (int64_t)e * NN;
+  float b1 = INFINITY, b2 = INFINITY;
+  int nb = 0;
+#pragma unroll 4
+  for (int n = 0; n < NN; ++n) {
+    float d = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const float t = xr[c] - __ldg(X32 + c * m.cstride + n);
+      d = fmaf(t, t, d);
+    }
+    if (d < b1) {
+      b2 = b1;
+      b1 = d;
+      nb = n;
+    } else if (d < b2) {
+      b2 = d;
+    }
+  }
+  float xm = 0.f;
+#pragma unroll
+  for (int c = 0; c < D; ++c) xm = fmaxf(xm, fabsf(xr[c]));
+  const float E = 2.3841858e-07f * (xm + __ldg(m.box32 + (int64_t)e * BOX32 + 18));
+  const float B1 = 2.f * sqrtf(D * b1) * E + D * E * E + 4.7683716e-07f * b1;
+  const float B2 = 2.f * sqrtf(D * b2) * E + D * E * E + 4.7683716e-07f * b2;
+  if (b2 - B2 > b1 + B1) return nb;
+  const double* X = m.coords + (int64_t)e * NN;
+  double best = INFINITY;
+  nb = 0;
+  for (int n = 0; n < NN; ++n) {
+    double dd = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const double t = __dsub_rn(xs[c], __ldg(X + c * m.cstride + n));
+      dd = __dadd_rn(dd, __dmul_rn(t, t));
+    }
+    if (dd < best) {
+      best = dd;
+      nb = n;
+    }
+  }
+  return nb;
+}
+
+template <int N, int DR, typename T>
+__device__ __forceinline__ void node_coords(const BasisTab& B, int n, T (&r)[DR]) {
+  const int idx[3] = {n % N, (n / N) % N, n / (N * N)};
+#pragma unroll
+  for (int j = 0; j < DR; ++j) {
+    T v = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i == idx[j]) v = TabOf<T>::z(B)[i];
+    r[j] = v;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ double aabb_scale(const DevMesh& m, int64_t e) {
+  double X = 0.0;
+#pragma unroll
+  for (int c = 0; c < 2 * D; ++c) X = fmax(X, fabs(__ldg(m.aabb + e * 2 * D + c)));
+  return X;
+}
+
+// Psi_L cell of x, or -1 when x lies outside the grid (then outside every
+// AABB) or has a non-finite coordinate.
+template <int D>
+__device__ __forceinline__ int64_t point_cell(const DevMesh& m, const double (&xs)[D]) {
+  int64_t cell = 0, mul = 1;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    if (!(xs[c] >= m.lo[c] && xs[c] <= m.hi[c])) return -1;
+    cell += mul * cell_coord(xs[c], m.lo[c], m.scale[c], m.NL);
+    mul *= m.NL;
+  }
+  return cell;
+}
+
+template <int DR>
+__device__ __forceinline__ void write_result(int64_t p, int code_, int e, const double (&r)[DR],
+                                             double d2, int* __restrict__ code, int* __restrict__ elem,
+                                             double* __restrict__ rout, double* __restrict__ dist2) {
+  code[p] = code_;
+  elem[p] = e;
+#pragma unroll
+  for (int j = 0; j < DR; ++j) rout[p * DR + j] = r[j];
+  dist2[p] = d2;
+}
+
+// ---- the trust-region step of Sec. 3.2.1 ------------------------------------
+
+template <int DR, typename T>
+__device__ __forceinline__ bool at_bound(const T (&r)[DR]) {
+  bool b = false;
+#pragma unroll
+  for (int j = 0; j < DR; ++j) b |= (r[j] == T(-1) || r[j] == T(1));
+  return b;
+}
+
+// Solves H_FF s_F = -g_F on the free coordinates (held ones get s = 0): the
+// held rows and columns are replaced by the identity, which leaves the free
+// block's leading minors unchanged.
+template <int DR, typename T>
+__device__ __forceinline__ bool masked_solve(const T (&H)[DR][DR], const bool (&held)[DR],
+                                             const T (&g)[DR], T (&s)[DR]) {
+  T A[DR][DR], b[DR];
+#pragma unroll
+  for (int j = 0; j < DR; ++j) {
+#pragma unroll
+    for (int k = 0; k < DR; ++k)
+      A[j][k] = (held[j] || held[k]) ? (j == k ? T(1) : T(0)) : H[j][k];
+    b[j] = held[j] ? T(0) : -g[j];
+  }
+  if (!spd_solve<DR, T>(A, b, s)) return false;
+#pragma unroll
+  for (int j = 0; j < DR; ++j)
+    if (held[j]) s[j] = T(0);
+  return true;
+}
+
+// Shared-memory slabs for the t-direction basis values of every thread of
+// the CTA (hexes only): 3N slots of kFindThreads values.
+template <int N, typename T>
+struct TSlots {
+  T* base;
+  __device__ __forceinline__ Slots<T> slot(int which) const { return Slots<T>{base + which * N * kFindThreads, kFindThreads}; }
+};
+
+// x(re) and, if WANT_G, G(re) of element data X: the uniform evaluation site.
+template <int N, int D, int DR, bool WANT_G, typename T>
+__device__ __forceinline__ void eval_xG(const T* __restrict__ X, int64_t cs, const BasisTab& B,
+                                        const T (&re)[DR], const TSlots<N, T>& ts, T* x, T* G) {
+  T ph[3][N], dph[3][N];
+#pragma unroll
+  for (int j = 0; j < DR; ++j) lagrange<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), re[j], ph[j], dph[j]);
+  if constexpr (DR == 3) {
+    const Slots<T> pt = ts.slot(0), dpt = ts.slot(1);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      pt(k) = ph[2][k];
+      dpt(k) = dph[2][k];
+    }
+    map_eval_rolled<N, D, WANT_G, T>(X, cs, ph, dph, pt, dpt, x, G);
+  } else {
+    T ph2[2][N], dph2[2][N];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        ph2[j][i] = ph[j][i];
+        dph2[j][i] = dph[j][i];
+      }
+    map_eval<N, 2, D, WANT_G, T>(X, cs, ph2, dph2, x, G);
+  }
+}
+
+// HS_jk = sum_c dx_c d2x_c/dr_j dr_k at r (the beta term of Eq. newton_hessian).
+template <int N, int D, int DR, typename T>
+__device__ void hess_term(const T* __restrict__ X, int64_t cs, const BasisTab& B, const T (&r)[DR],
+                          const T (&dx)[D], const TSlots<N, T>& ts, T (&HS)[DR][DR]) {
+  T S[D * DR * DR];
+  if constexpr (DR == 3) {
+    T ph[3][N], dph[3][N], d2ph[3][N];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lagrange2<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), r[j], ph[j], dph[j], d2ph[j]);
+    const Slots<T> pt = ts.slot(0), dpt = ts.slot(1), d2pt = ts.slot(2);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      pt(k) = ph[2][k];
+      dpt(k) = dph[2][k];
+      d2pt(k) = d2ph[2][k];
+    }
+    map_hess_rolled<N, D, T>(X, cs, ph, dph, d2ph, pt, dpt, d2pt, S);
+  } else {
+    T ph[DR][N], dph[DR][N], d2ph[DR][N];
+#pragma unroll
+    for (int j = 0; j < DR; ++j) lagrange2<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), r[j], ph[j], dph[j], d2ph[j]);
+    map_hess<N, DR, D, T>(X, cs, ph, dph, d2ph, S);
+  }
+#pragma unroll
+  for (int j = 0; j < DR; ++j)
+#pragma unroll
+    for (int k = 0; k < DR; ++k) {
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) s += dx[c] * S[(c * DR + j) * DR + k];
+      HS[j][k] = s;
+    }
+}
+
+// Gradient g = -G^T dx, held set, Hessian G^T G - beta HS, masked solve with
+// the fallbacks (beta = 0 block, then no step), clip to [-alpha, alpha] and
+// projection on [-1,1].  Returns |dr|_inf of the projected step.
+template <int D, int DR, typename T>
+__device__ __forceinline__ T newton_step(const T (&G)[D * DR], const T (&dx)[D], const T (&r)[DR],
+                                         T alpha, bool beta, const T (&HS)[DR][DR], T (&rn)[DR],
+                                         T (&ds)[DR], bool& clipped, bool& used_beta) {
+  T g[DR], HGN[DR][DR], H[DR][DR], step[DR];
+  bool held[DR];
+#pragma unroll
+  for (int j = 0; j < DR; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) s -= G[c * DR + j] * dx[c];
+    g[j] = s;
+    held[j] = (r[j] == T(-1) && s > T(0)) || (r[j] == T(1) && s < T(0));
+  }
+#pragma unroll
+  for (int j = 0; j < DR; ++j)
+#pragma unroll
+    for (int k = 0; k < DR; ++k) {
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) s += G[c * DR + j] * G[c * DR + k];
+      HGN[j][k] = s;
+      H[j][k] = beta ? s - HS[j][k] : s;
+    }
+  used_beta = beta;
+  bool ok = masked_solve<DR, T>(H, held, g, step);
+  if (!ok && beta) {
+    used_beta = false;
+    ok = masked_solve<DR, T>(HGN, held, g, step);
+  }
+  if (!ok) {
+    used_beta = false;
+#pragma unroll
+    for (int j = 0; j < DR; ++j) step[j] = T(0);
+  }
+  T mx = T(0);
+  clipped = false;
+#pragma unroll
+  for (int j = 0; j < DR; ++j) {
+    T s = step[j];
+    if (s > alpha) {
+      s = alpha;
+      clipped = true;
+    }
+    if (s < -alpha) {
+      s = -alpha;
+      clipped = true;
+    }
+    T v = r[j] + s;
+    if (v > T(1)) v = T(1);
+    if (v < T(-1)) v = T(-1);
+    rn[j] = v;
+    ds[j] = v - r[j];
+    mx = fmax(mx, fabs(ds[j]));
+  }
+  return mx;
+}
+
+// -2 g.dr - dr^T H dr with H = G^T G (beta = 0: the same value as
+// |dx|^2 - |dx - G dr|^2) or G^T G - HS (beta = 1).
+template <int D, int DR, typename T>
+__device__ __forceinline__ T predicted_decrease(const T (&G)[D * DR], const T (&dx)[D], const T (&ds)[DR],
+                                                bool used_beta, const T (&HS)[DR][DR]) {
+  T lin = T(0), quad = T(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    T gd = T(0);
+#pragma unroll
+    for (int j = 0; j < DR; ++j) gd += G[c * DR + j] * ds[j];
+    lin -= gd * dx[c];  // g.ds with g = -G^T dx
+    quad += gd * gd;
+  }
+  if (used_beta) {
+#pragma unroll
+    for (int j = 0; j < DR; ++j)
+#pragma unroll
+      for (int k = 0; k < DR; ++k) quad -= ds[j] * HS[j][k] * ds[k];
+  }
+  return T(-2) * lin - quad;
+}
+
+// |dx - G dr|^2: the distance after the last (sub-tolerance) step.
+template <int D, int DR, typename T>
+__device__ __forceinline__ T model_dist2(const T (&G)[D * DR], const T (&dx)[D], const T (&ds)[DR]) {
+  T f = T(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    T t = dx[c];
+#pragma unroll
+    for (int j = 0; j < DR; ++j) t -= G[c * DR + j] * ds[j];
+    f += t * t;
+  }
+  return f;
+}
+
+// Ratio test of Sec. 3.2.1 with the rounding-level acceptance; updates alpha.
+template <typename T>
+__device__ __forceinline__ bool trial_accepts(T F, T Fn, T pred, bool clipped, T xscale, T& alpha,
+                                              T tau_factor = T(1e-12)) {
+  const T decr = F - Fn;
+  const T tau = tau_factor * xscale * sqrt(F);
+  if (!clipped && pred < tau) return true;
+  if (decr >= T(0.9) * pred) {
+    alpha *= T(2);
+    return true;
+  }
+  if (decr >= T(0.01) * pred) return true;
+  alpha *= T(0.25);
+  return false;
+}
+
+int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
+             int* elem, double* r, double* dist2, unsigned long long* stats, cudaStream_t st);
+int find_mixed(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem, double* r,
+               double* dist2, unsigned long long* stats, cudaStream_t st);
+
+}  // namespace fp

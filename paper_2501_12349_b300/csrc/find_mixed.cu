@@ -1,0 +1,332 @@
+// Mixed-precision find (FP_MIXED): FP32 box filter and early Newton
+// steps, FP64 final steps, residual check and ill-conditioned solves.
+//
+// Kernel k_find_mixed, per point (lanes refill as in the FP64 kernel):
+//  1. Psi_L cell in FP64; candidates from the certified FP32 box tests
+//     (decisions equal the FP64 ones; inside the margin the FP64 test runs).
+//  2. Per candidate, trust-region Newton of Sec. 3.2.1 in FP32 on the
+//     element's FP32 coordinates taken relative to its reference point
+//     (values O(h), so the FP32 Jacobian keeps ~1e-7 relative accuracy).
+//  3. A candidate whose FP32 iteration converged strictly inside the element
+//     is parked for FP64 refinement: x(r) in FP64, the Gauss-Newton step
+//     solved in FP64 with the FP32 Jacobian, repeated until the step is below
+//     the Newton tolerance (typically two FP64 evaluations).  Parked lanes
+//     wait until most of their warp is parked, so the FP64 work runs with
+//     nearly full warps.
+//  4. A candidate the FP32 iteration leaves clearly outside (on the boundary
+//     with a distance far above FP32 rounding) is BORDER, as FP64 would find;
+//     the search continues with the next candidate.
+//  5. Anything else — a point with only BORDER candidates (its answer is the
+//     closest BORDER candidate, needing FP64 distances), a refinement that
+//     leaves the element, an ill-conditioned Jacobian, an FP32 iteration at
+//     its rounding floor near a face — goes to a queue in scratch memory, and
+//     k_find_f64 then runs the full FP64 path on the queued points.
+// Points with no candidate are NOT_FOUND straight away.
+#include "find_f64.cuh"
+
+namespace fp {
+namespace {
+
+enum : int { X_IDLE = 0, X_SCAN = 1, X_NEWTON = 2, X_RESTORE = 3, X_PARK = 4, X_DONE = 5 };
+enum : int { X_INIT = 1, X_TRIAL = 2, X_REST = 3 };
+
+constexpr float kTol32 = 2e-6f;    // FP32 phase: stop when |dr|_inf < kTol32
+constexpr float kTau32 = 1e-5f;    // FP32 rounding-level acceptance factor
+constexpr float kBorder32 = 1e-4f; // "clearly outside": distance > kBorder32 * Xrel
+constexpr int kPark = 28;          // run the FP64 refinement with >= kPark lanes parked
+constexpr int kMaxRefine = 4;
+
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kFindThreads, 2)
+    k_find_mixed(const DevMesh m, const BasisTab B, const double* __restrict__ pts, int64_t n,
+                 int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
+                 double* __restrict__ dist2, int* __restrict__ queue, int* __restrict__ qcount,
+                 unsigned long long* stats) {
+  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  __shared__ double s_slab64[DR == 3 ? 2 * N * kFindThreads : 1];
+  __shared__ float s_slab32[DR == 3 ? 3 * N * kFindThreads : 1];
+  const TSlots<N, double> ts64{s_slab64};
+  const TSlots<N, float> ts32{s_slab32};
+  __shared__ unsigned long long s_next;
+  if (threadIdx.x == 0) s_next = 0;
+  __syncthreads();
+  Counters cnt;
+  const int64_t nchunks = (n + 31) / 32;
+  int mode = X_IDLE, etype = X_INIT;
+  int64_t pi = 0;
+  double xs[D];
+  float x32[D], xr[D];
+  int q = 0, qend = 0, e = -1, l = 0, nref = 0;
+  bool has_border = false, clipped = false;
+  float r[DR], rn[DR], dx[D], G[D * DR];
+  float alpha = 1.f, F = 0.f, pred = 0.f, xrel = 1.f;
+  double r64[DR];
+  unsigned guard = 0;
+#pragma unroll
+  for (int j = 0; j < DR; ++j) r[j] = rn[j] = 0.f, r64[j] = 0.0;
+
+  while (true) {
+    bool need = false;
+    while (mode != X_DONE && mode != X_PARK && !need) {
+      if (++guard > (1u << 26)) {
+        record_status(m.status, FP_DEV_SPIN_CAP);
+        mode = X_DONE;
+        break;
+      }
+      if (mode == X_IDLE) {
+        const unsigned long long s = atomicAdd(&s_next, 1ull);
+        const int64_t chunk = (int64_t)(s >> 5) * gridDim.x + blockIdx.x;
+        if (chunk >= nchunks) {
+          mode = X_DONE;
+          break;
+        }
+        pi = chunk * 32 + (int64_t)(s & 31);
+        if (pi >= n) continue;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          xs[c] = __ldg(pts + pi * D + c);
+          x32[c] = (float)xs[c];
+        }
+        has_border = false;
+        const int64_t cell = point_cell<D>(m, xs);
+        if (cell < 0) {
+          const double z0[DR] = {};
+          write_result<DR>(pi, FP_NOT_FOUND, -1, z0, INFINITY, code, elem, rout, dist2);
+          continue;
+        }
+        q = __ldg(m.cell_start + cell);
+        qend = __ldg(m.cell_start + cell + 1);
+        mode = X_SCAN;
+      }
+      if (mode == X_SCAN) {
+        e = next_candidate<D>(m, xs, x32, q, qend, cnt);
+        if (e < 0) {
+          if (has_border) {
+            queue[atomicAdd(qcount, 1)] = (int)pi;
+            ++cnt.v[6];
+          } else {
+            const double z0[DR] = {};
+            write_result<DR>(pi, FP_NOT_FOUND, -1, z0, INFINITY, code, elem, rout, dist2);
+          }
+          mode = X_IDLE;
+          continue;
+        }
+        ++cnt.v[0];
+        rel_point<D>(m, e, xs, xr);
+        xrel = __ldg(m.box32 + (int64_t)e * BOX32 + 18);
+        // closest node in FP32 (the start only changes the path, not the
+        // converged result, and FP64 decides everything that matters)
+        const float* X32 = m.coords32 + (int64_t)e * NN;
+        float b1 = INFINITY;
+        int nb = 0;
+#pragma unroll 4
+        for (int nn = 0; nn < NN; ++nn) {
+          float d = 0.f;
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const float t = xr[c] - __ldg(X32 + c * m.cstride + nn);
+            d = fmaf(t, t, d);
+          }
+          if (d < b1) {
+            b1 = d;
+            nb = nn;
+          }
+        }
+        node_coords<N, DR, float>(B, nb, r);
+        etype = X_INIT;
+        need = true;
+        break;
+      }
+      if (mode == X_RESTORE) {
+        etype = X_REST;
+        need = true;
+        break;
+      }
+      // X_NEWTON: one FP32 step
+      bool done = false, converged = false;
+      if (l >= m.max_iter) {
+        done = true;
+      } else {
+        const bool beta = (l > 0) && at_bound<DR>(r);
+        float HS[DR][DR];
+        if (beta) hess_term<N, D, DR, float>(m.coords32 + (int64_t)e * NN, m.cstride, B, r, dx, ts32, HS);
+        float ds[DR];
+        bool used_beta;
+        const float mx = newton_step<D, DR, float>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
+        if (mx < kTol32) {
+          F = model_dist2<D, DR, float>(G, dx, ds);
+#pragma unroll
+          for (int j = 0; j < DR; ++j) r[j] = rn[j];
+          ++cnt.v[1];
+          done = converged = true;
+        } else {
+          pred = predicted_decrease<D, DR, float>(G, dx, ds, used_beta, HS);
+          if (!(pred > 0.f)) {
+            done = true;
+          } else {
+            ++cnt.v[1];
+            if (beta) ++cnt.v[3];
+            etype = X_TRIAL;
+            need = true;
+          }
+        }
+      }
+      if (done) {
+        bool inside = true;
+#pragma unroll
+        for (int j = 0; j < DR; ++j) inside &= fabsf(r[j]) < 1.f;
+        const float far2 = (kBorder32 * xrel) * (kBorder32 * xrel);
+        const float dtol = (float)m.dist_tol;
+        if (converged && inside && (DR == D || F < 0.5f * dtol)) {
+#pragma unroll
+          for (int j = 0; j < DR; ++j) r64[j] = (double)r[j];
+          nref = 0;
+          mode = X_PARK;
+        } else if (F > far2 && (!inside || (DR < D && converged && F > 2.f * dtol))) {
+          has_border = true;
+          mode = X_SCAN;
+        } else {
+          queue[atomicAdd(qcount, 1)] = (int)pi;
+          ++cnt.v[6];
+          mode = X_IDLE;
+        }
+      }
+    }
+    const unsigned parked = __ballot_sync(0xffffffffu, mode == X_PARK);
+    const unsigned busy = __ballot_sync(0xffffffffu, need);
+    if (parked == 0 && busy == 0) {
+      if (__all_sync(0xffffffffu, mode == X_DONE)) break;
+      continue;
+    }
+    // ---- FP64 refinement, warp-batched --------------------------------------
+    if ((__popc(parked) >= kPark || busy == 0) && mode == X_PARK) {
+      ++cnt.v[4];
+      double xv[D], dxd[D], Gd[D * DR];
+      eval_xG<N, D, DR, false, double>(m.coords + (int64_t)e * NN, m.cstride, B, r64, ts64, xv, nullptr);
+#pragma unroll
+      for (int c = 0; c < D; ++c) dxd[c] = xs[c] - xv[c];
+#pragma unroll
+      for (int q2 = 0; q2 < D * DR; ++q2) Gd[q2] = (double)G[q2];
+      // Gauss-Newton step in FP64: (G^T G) s = G^T dx
+      double H[DR][DR], b[DR], s[DR];
+#pragma unroll
+      for (int j = 0; j < DR; ++j) {
+        double t = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) t += Gd[c * DR + j] * dxd[c];
+        b[j] = t;
+#pragma unroll
+        for (int k = 0; k < DR; ++k) {
+          double u = 0.0;
+#pragma unroll
+          for (int c = 0; c < D; ++c) u += Gd[c * DR + j] * Gd[c * DR + k];
+          H[j][k] = u;
+        }
+      }
+      double dprod = 1.0;
+#pragma unroll
+      for (int j = 0; j < DR; ++j) dprod *= H[j][j];
+      double det = (DR == 2) ? H[0][0] * H[1][1] - H[0][1] * H[1][0]
+                             : H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
+                                   H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+                                   H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+      bool ok = spd_solve<DR, double>(H, b, s) && det > 1e-8 * dprod;
+      bool inside = ok;
+      double mx = 0.0, rnn[DR];
+#pragma unroll
+      for (int j = 0; j < DR; ++j) {
+        rnn[j] = r64[j] + s[j];
+        inside &= fabs(rnn[j]) < 1.0;
+        mx = fmax(mx, fabs(s[j]));
+      }
+      if (!inside) {
+        queue[atomicAdd(qcount, 1)] = (int)pi;
+        ++cnt.v[6];
+        mode = X_IDLE;
+      } else if (mx < m.newton_tol) {
+        double f = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          double t = dxd[c];
+#pragma unroll
+          for (int j = 0; j < DR; ++j) t -= Gd[c * DR + j] * s[j];
+          f += t * t;
+        }
+        if (DR < D && !(f < m.dist_tol)) {
+          queue[atomicAdd(qcount, 1)] = (int)pi;
+          ++cnt.v[6];
+        } else {
+          write_result<DR>(pi, FP_INTERIOR, e, rnn, f, code, elem, rout, dist2);
+        }
+        mode = X_IDLE;
+      } else if (++nref >= kMaxRefine) {
+        queue[atomicAdd(qcount, 1)] = (int)pi;
+        ++cnt.v[6];
+        mode = X_IDLE;
+      } else {
+#pragma unroll
+        for (int j = 0; j < DR; ++j) r64[j] = rnn[j];
+      }
+    }
+    // ---- FP32 evaluation -----------------------------------------------------
+    if (need) {
+      float re[DR];
+#pragma unroll
+      for (int j = 0; j < DR; ++j) re[j] = (etype == X_TRIAL) ? rn[j] : r[j];
+      float xv[D];
+      eval_xG<N, D, DR, true, float>(m.coords32 + (int64_t)e * NN, m.cstride, B, re, ts32, xv, G);
+      float Fn = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        dx[c] = xr[c] - xv[c];
+        Fn = fmaf(dx[c], dx[c], Fn);
+      }
+      if (etype == X_TRIAL) {
+        ++l;
+        if (trial_accepts<float>(F, Fn, pred, clipped, xrel, alpha, kTau32)) {
+#pragma unroll
+          for (int j = 0; j < DR; ++j) r[j] = rn[j];
+          F = Fn;
+          mode = X_NEWTON;
+        } else {
+          ++cnt.v[2];
+          mode = X_RESTORE;
+        }
+      } else {
+        if (etype == X_INIT) {
+          alpha = 1.f;
+          l = 0;
+        }
+        F = Fn;
+        mode = X_NEWTON;
+      }
+    }
+  }
+  cnt.flush(stats);
+}
+
+}  // namespace
+
+int find_mixed(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem, double* r,
+               double* dist2, unsigned long long* stats, cudaStream_t st) {
+  int* queue = nullptr;
+  if (cudaMallocAsync((void**)&queue, sizeof(int) * (size_t)(n + 1), st) != cudaSuccess) return FP_ENOMEM;
+  int* qcount = queue + n;
+  int rc = FP_OK;
+  if (cudaMemsetAsync(qcount, 0, sizeof(int), st) != cudaSuccess) rc = FP_ELAUNCH;
+  const DevMesh v = m->view();
+  if (rc == FP_OK)
+    rc = dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+      constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
+      const int blocks = persistent_blocks(n, 2);
+      k_find_mixed<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, n, code, elem, r,
+                                                              dist2, queue, qcount, stats);
+      k_find_f64<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount, code,
+                                                            elem, r, dist2, stats);
+      return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+    });
+  cudaFreeAsync(queue, st);
+  return rc;
+}
+
+}  // namespace fp

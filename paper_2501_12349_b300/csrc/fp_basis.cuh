@@ -203,6 +203,108 @@ __device__ __forceinline__ void map_hess(const T* __restrict__ X, int64_t cs, co
   }
 }
 
+// Per-thread slots in shared memory, column-major ([slot][blockDim.x]) so
+// that a warp reading slot k touches consecutive words.
+template <typename T>
+struct Slots {
+  T* base;
+  int stride;
+  __device__ __forceinline__ T& operator()(int k) const { return base[k * stride + threadIdx.x]; }
+};
+
+// As map_eval for hexes (DR == 3), with the outer t-loop rolled: the t-basis
+// values come from shared-memory slots pt(k) = phi_k(t), dpt(k) = phi_k'(t),
+// so the contraction inlines as one N^2 body instead of N^3 (a much smaller
+// kernel: the FP64 find kernels were instruction-fetch bound unrolled).
+template <int N, int D, bool WANT_G, typename T>
+__device__ __forceinline__ void map_eval_rolled(const T* __restrict__ X, int64_t cs,
+                                                const T (&ph)[3][N], const T (&dph)[3][N],
+                                                const Slots<T>& pt, const Slots<T>& dpt, T* x, T* G) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const T* xe = X + c * cs;
+    T xv = T(0), g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      T ak = T(0), bk = T(0), ck = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        T a = T(0), b = T(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const T v = ldg(xe + (k * N + j) * N + i);
+          a = fma(v, ph[0][i], a);
+          if (WANT_G) b = fma(v, dph[0][i], b);
+        }
+        ak = fma(a, ph[1][j], ak);
+        if (WANT_G) {
+          bk = fma(b, ph[1][j], bk);
+          ck = fma(a, dph[1][j], ck);
+        }
+      }
+      const T tk = pt(k);
+      xv = fma(ak, tk, xv);
+      if (WANT_G) {
+        g0 = fma(bk, tk, g0);
+        g1 = fma(ck, tk, g1);
+        g2 = fma(ak, dpt(k), g2);
+      }
+    }
+    x[c] = xv;
+    if (WANT_G) {
+      G[c * 3 + 0] = g0;
+      G[c * 3 + 1] = g1;
+      G[c * 3 + 2] = g2;
+    }
+  }
+}
+
+// map_hess for hexes with the t-loop rolled (t-basis values and their first
+// and second derivatives in slots pt, dpt, d2pt).
+template <int N, int D, typename T>
+__device__ __forceinline__ void map_hess_rolled(const T* __restrict__ X, int64_t cs,
+                                                const T (&ph)[3][N], const T (&dph)[3][N],
+                                                const T (&d2ph)[3][N], const Slots<T>& pt,
+                                                const Slots<T>& dpt, const Slots<T>& d2pt, T* S) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const T* xe = X + c * cs;
+    T rr = 0, rs = 0, rt = 0, ss = 0, st = 0, tt = 0;
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      T p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0, p6 = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        T a = 0, b = 0, c2 = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const T v = ldg(xe + (k * N + j) * N + i);
+          a = fma(v, ph[0][i], a);
+          b = fma(v, dph[0][i], b);
+          c2 = fma(v, d2ph[0][i], c2);
+        }
+        p1 = fma(c2, ph[1][j], p1);
+        p2 = fma(b, dph[1][j], p2);
+        p3 = fma(b, ph[1][j], p3);
+        p4 = fma(a, d2ph[1][j], p4);
+        p5 = fma(a, dph[1][j], p5);
+        p6 = fma(a, ph[1][j], p6);
+      }
+      const T tk = pt(k), dtk = dpt(k), d2tk = d2pt(k);
+      rr = fma(p1, tk, rr);
+      rs = fma(p2, tk, rs);
+      rt = fma(p3, dtk, rt);
+      ss = fma(p4, tk, ss);
+      st = fma(p5, dtk, st);
+      tt = fma(p6, d2tk, tt);
+    }
+    T* Sc = S + c * 9;
+    Sc[0] = rr; Sc[1] = rs; Sc[2] = rt;
+    Sc[3] = rs; Sc[4] = ss; Sc[5] = st;
+    Sc[6] = rt; Sc[7] = st; Sc[8] = tt;
+  }
+}
+
 // Solves A s = b for a symmetric DR x DR matrix by cofactors when A is
 // positive definite (all leading principal minors > 0, the same sign test as
 // the pivots of a Cholesky factorisation); returns false otherwise.

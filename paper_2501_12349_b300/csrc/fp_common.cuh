@@ -31,6 +31,16 @@
 
 namespace fp {
 
+// Record of one element in DevMesh::box32: lo[3] hi[3] c[3] A[9] Xrel pad
+// (floats); Xrel bounds |x - x_ref| over the element (largest AABB half-width).
+constexpr int BOX32 = 20;
+
+// Reference point of element e: the centre of its expanded AABB, computed
+// with the same rounded operations at setup and at find.
+__device__ __forceinline__ double elem_ref(const double* __restrict__ aabb, int d, int64_t e, int c) {
+  return (aabb[e * 2 * d + c] + aabb[e * 2 * d + d + c]) * 0.5;
+}
+
 // GLL nodes z_i and barycentric weights w_i = 1 / prod_{m!=i} (z_i - z_m) of
 // one order, passed by value so the kernels read them from the constant bank.
 struct BasisTab {
@@ -43,11 +53,13 @@ struct BasisTab {
 // Everything a find / eval kernel reads about a mesh (passed by value).
 struct DevMesh {
   const double* coords;    // [d][NE][ne]
-  const float* coords32;   // FP32 copy (mixed path)
+  const float* coords32;   // FP32 copy relative to the element reference point
+                           // (elem_ref): fl(x - x_ref), so values are O(h)
   const double* aabb;      // [NE][2d], expanded
   const double* obb_c;     // [NE][d]
   const double* obb_A;     // [NE][d][d]
-  const float* box32;      // [NE][BOX32_STRIDE]: outward-rounded FP32 boxes (mixed path)
+  const float* box32;      // [NE][BOX32]: FP32 copy of aabb, obb_c, obb_A and the
+                           // coordinate scale X (max |aabb|), for certified FP32 tests
   const int* cell_start;   // [ncell + 1]
   const int* cell_elems;   // [nnz]
   int64_t NE;

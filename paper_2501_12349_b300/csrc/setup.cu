@@ -555,10 +555,39 @@ __global__ void k_grid_sort(const int* __restrict__ start, int64_t ncell, int* _
   }
 }
 
-__global__ void k_to_float(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = (float)x[i];
+// coords32[c][e][n] = fl32(coords[c][e][n] - x_ref(e)_c)
+__global__ void k_coords32(const double* __restrict__ x, const double* __restrict__ aabb, int d,
+                           int64_t NE, int ne, float* __restrict__ y) {
+  const int64_t total = (int64_t)d * NE * ne;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ce = i / ne;
+    const int c = (int)(ce / NE);
+    const int64_t e = ce % NE;
+    y[i] = (float)(x[i] - elem_ref(aabb, d, e, c));
+  }
+}
+
+// FP32 record per element (layout fp::BOX32): lo[3] hi[3] c[3] A[3][3] Xrel
+// pad, rounded to nearest (the certified FP32 tests carry their own
+// margins); Xrel = largest AABB half-width, slightly enlarged, bounds
+// |x - x_ref| over the element.
+__global__ void k_box32(const double* __restrict__ aabb, const double* __restrict__ obb_c,
+                        const double* __restrict__ obb_A, int64_t NE, int d, float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < NE;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float* o = out + e * BOX32;
+    for (int i = 0; i < BOX32; ++i) o[i] = 0.f;
+    double X = 0.0;
+    for (int c = 0; c < d; ++c) {
+      o[c] = (float)aabb[e * 2 * d + c];
+      o[3 + c] = (float)aabb[e * 2 * d + d + c];
+      o[6 + c] = (float)obb_c[e * d + c];
+      X = fmax(X, 0.5 * (aabb[e * 2 * d + d + c] - aabb[e * 2 * d + c]));
+      for (int k = 0; k < d; ++k) o[9 + c * 3 + k] = (float)obb_A[(e * d + c) * d + k];
+    }
+    o[18] = (float)(X * (1.0 + 1e-6));
+  }
 }
 
 template <typename T>
@@ -590,8 +619,6 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st);
 
 }  // namespace
 }  // namespace fp
-
-int fp_mixed_prepare(fp_mesh_s* m, cudaStream_t st);  // find.cu
 
 fp::DevMesh fp_mesh_s::view() const {
   fp::DevMesh v;
@@ -711,6 +738,12 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
     cudaMemsetAsync(counts, 0, ncell * sizeof(int), st);
     k_grid_scatter<1><<<eb, 256, 0, st>>>(m->aabb, m->NE, g, counts, m->cell_start, m->cell_elems);
     k_grid_sort<<<grid_for(ncell, 256, 148 * 16), 256, 0, st>>>(m->cell_start, ncell, m->cell_elems);
+    if ((rc = dev_alloc(&m->box32, (size_t)m->NE * BOX32, &m->bytes)) != FP_OK) {
+      cudaFree(counts);
+      break;
+    }
+    k_box32<<<grid_for(m->NE, 256, 148 * 16), 256, 0, st>>>(m->aabb, m->obb_c, m->obb_A, m->NE, m->d,
+                                                            m->box32);
     ce = cudaStreamSynchronize(st);
     cudaFree(counts);
     if (ce != cudaSuccess) rc = FP_ELAUNCH;
@@ -777,9 +810,9 @@ extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int6
       rc = FP_ELAUNCH;
       break;
     }
-    k_to_float<<<grid_for((int64_t)nc, 256, 148 * 16), 256, 0, st>>>(m->coords, (int64_t)nc, m->coords32);
     if ((rc = build_boxes_and_grid(m, st)) != FP_OK) break;
-    if ((rc = fp_mixed_prepare(m, st)) != FP_OK) break;
+    k_coords32<<<grid_for((int64_t)nc, 256, 148 * 16), 256, 0, st>>>(m->coords, m->aabb, d, NE, m->ne,
+                                                                    m->coords32);
     int hstat = 0;
     if (cudaMemcpyAsync(&hstat, m->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {

@@ -1,18 +1,22 @@
 """Shared comparison of GPU results with the FP64 oracle.
 
 Tolerances (FP64 path): element id and code identical; r within 1e-10;
-dist2 within 1e-12 relative + 1e-24 absolute; interpolated values within
-1e-12 relative to max(|oracle value|, max |nodal value| of the element).
+interpolated values within 1e-12 relative to max(|oracle value|, max |nodal
+value| of the element); dist2 within 1e-12 relative + 1e-14 X sqrt(dist2)
++ 1e-24 absolute.  The middle term follows from the arithmetic: dist2 =
+|dx|^2 with dx = x* - x(r) carrying a rounding error of a few ulp of the
+coordinates X (X = 1 for these meshes), so |d dist2| ~ 2 |dx| eps X.
 
 Where several answers are correct the comparison checks what is unique: a
 BORDER point whose closest boundary point is shared by two candidate
 elements has two valid element ids with equal dist2, so a differing
-BORDER element is accepted only when both dist2 values agree to 1e-12.
+BORDER element is accepted only when both dist2 values agree within the
+dist2 tolerance.
 """
 import numpy as np
 
 R_TOL = 1e-10
-D2_REL, D2_ABS = 1e-12, 1e-24
+D2_REL, D2_X, D2_ABS = 1e-12, 1e-14, 1e-24
 U_REL = 1e-12
 
 
@@ -20,11 +24,11 @@ def to_np(t):
     return t.detach().cpu().numpy()
 
 
-def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label=""):
+def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label="", xscale=1.0):
     oc, oe, orr, od = oracle_out
     gc, ge, gr, gd = gpu_out
     mism = (oc != gc) | (oe != ge)
-    tie = mism & (oc == 1) & (gc == 1) & (np.abs(od - gd) <= D2_REL * np.abs(od) + D2_ABS)
+    tie = mism & (oc == 1) & (gc == 1) & (np.abs(od - gd) <= D2_REL * np.abs(od) + D2_X * xscale * np.sqrt(np.abs(od)) + D2_ABS)
     bad = np.flatnonzero(mism & ~tie)
     assert bad.size == 0, (
         f"{label}: {bad.size} code/elem mismatches, e.g. idx {bad[:5]}: oracle "
@@ -33,8 +37,11 @@ def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label=""):
     if same.any():
         dr = np.max(np.abs(orr[same] - gr[same]))
         assert dr <= r_tol, f"{label}: max |dr| = {dr:.3e}"
-        dd = np.abs(od[same] - gd[same]) - (D2_REL * np.abs(od[same]) + D2_ABS)
-        assert np.max(dd) <= 0, f"{label}: dist2 mismatch {np.max(dd):.3e}"
+        tol = D2_REL * np.abs(od[same]) + D2_X * xscale * np.sqrt(np.abs(od[same])) + D2_ABS
+        dd = np.abs(od[same] - gd[same]) - tol
+        k = int(np.argmax(dd))
+        assert dd[k] <= 0, (f"{label}: dist2 mismatch {dd[k]:.3e} over tolerance at "
+                            f"oracle {od[same][k]:.6e} gpu {gd[same][k]:.6e} code {oc[same][k]}")
     nf = oc == 2
     assert np.all(ge[nf] == -1) and np.all(np.isinf(gd[nf])) and np.all(gr[nf] == 0)
     return {"n": len(oc), "ties": int(tie.sum()), "codes": np.bincount(gc, minlength=3).tolist()}
