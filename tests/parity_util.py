@@ -28,7 +28,8 @@ def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label="", xscale=1.0):
     oc, oe, orr, od = oracle_out
     gc, ge, gr, gd = gpu_out
     mism = (oc != gc) | (oe != ge)
-    tie = mism & (oc == 1) & (gc == 1) & (np.abs(od - gd) <= D2_REL * np.abs(od) + D2_X * xscale * np.sqrt(np.abs(od)) + D2_ABS)
+    with np.errstate(invalid="ignore"):
+        tie = mism & (oc == 1) & (gc == 1) & (np.abs(od - gd) <= D2_REL * np.abs(od) + D2_X * xscale * np.sqrt(np.abs(od)) + D2_ABS)
     bad = np.flatnonzero(mism & ~tie)
     assert bad.size == 0, (
         f"{label}: {bad.size} code/elem mismatches, e.g. idx {bad[:5]}: oracle "
