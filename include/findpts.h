@@ -122,6 +122,28 @@ int fp_findpts_stats(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
                      int32_t* elem, double* r, double* dist2, uint64_t* stats_dev,
                      void* stream);
 
+/* Mixed-precision find that allocates no device memory.  The paper has no
+ * counterpart: it is the FP_MIXED algorithm of fp_findpts, for callers that
+ * cannot let a library call cudaMalloc — solvers that reserve the GPU's
+ * memory up front and run under a hard budget, and code that must not see
+ * the implicit synchronisation or the possible failure of an allocation in
+ * the middle of a time step.  Its scratch (the queue of points passed from
+ * the FP32 kernel to the FP64 kernel) is a fixed array inside the library of
+ * FP_NOALLOC_MAX_POINTS + 1 ints (4 MiB), held on every GPU that loads the
+ * library until the process exits.
+ *   Arguments, layouts and outputs as fp_findpts; the mesh's precision
+ *   setting is ignored (always FP_MIXED).  n > FP_NOALLOC_MAX_POINTS is
+ *   rejected with FP_EINVAL before anything runs; split larger sets.
+ *   The first call on a device looks up the array's device address (a
+ *   one-time set-up per device, with that device current); make that first
+ *   call before any stream capture.
+ *   All calls share the one array: calls that can overlap on the GPU (on
+ *   different streams, or from different threads) race and must be
+ *   serialised by the caller.  Each call clears the queue's counter. */
+#define FP_NOALLOC_MAX_POINTS (1 << 20)
+int fp_findpts_mixed_noalloc(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
+                             int32_t* elem, double* r, double* dist2, void* stream);
+
 /* Interpolate (Sec. 3.3): out[c][p] = u_c(r_p) in element elem_p for the
  * nc components of field_dev ([nc][NE][N^dr] FP64, device, same node layout
  * as the coordinates); 0 where code == FP_NOT_FOUND.  The same find output

@@ -190,6 +190,24 @@ def fp_alu_peak(which: int, iters: int = 4000, stream=None) -> float:
     return g.value
 
 
+FP_NOALLOC_MAX_POINTS = 1 << 20
+
+
+def fp_findpts_mixed_noalloc(mesh, pts, code, elem, r, dist2, stream=None) -> None:
+    """Mixed-precision find that allocates no device memory (at most
+    FP_NOALLOC_MAX_POINTS points per call; calls that overlap on the GPU
+    race on the library's one scratch array)."""
+    import torch
+    f = lib().fp_findpts_mixed_noalloc
+    f.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
+    f.restype = _int
+    n = pts.shape[0] if pts.dim() > 0 else 0
+    _check("fp_findpts_mixed_noalloc", f(
+        mesh, _ptr(pts, torch.float64, "pts"), n, _ptr(code, torch.int32, "code"),
+        _ptr(elem, torch.int32, "elem"), _ptr(r, torch.float64, "r"),
+        _ptr(dist2, torch.float64, "dist2"), _stream(stream)))
+
+
 class Mesh:
     """Owns an fp_mesh handle; allocates outputs as torch tensors."""
 

@@ -330,3 +330,24 @@ int find_mixed(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int*
 }
 
 }  // namespace fp
+
+namespace fp {
+
+// The two launches of the mixed path with a caller-provided queue
+// (capacity >= n entries) and zeroed counter; allocates nothing.
+int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem,
+                            double* r, double* dist2, int* queue, int* qcount,
+                            unsigned long long* stats, cudaStream_t st) {
+  const DevMesh v = m->view();
+  return dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+    constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
+    const int blocks = persistent_blocks(n, 2);
+    k_find_mixed<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, n, code, elem, r, dist2,
+                                                            queue, qcount, stats);
+    k_find_f64<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount, code,
+                                                          elem, r, dist2, stats);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+  });
+}
+
+}  // namespace fp
