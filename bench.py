@@ -218,6 +218,69 @@ def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist):
     return res
 
 
+def batch_block(fp, W, torch, dev, st, flush, args):
+    """The 64-mesh workload (quads, hexes, sphere/torus surfaces, p = 2..7,
+    1e3-5e4 elements, 1e3-1e6 points each, scalar fields): one autotuned
+    graph launch per run, against the same work issued as separate per-mesh
+    fp_findpts + fp_eval calls; FP64 and mixed precision."""
+    t0 = time.perf_counter()
+    ws = W.config4()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    meshes = [fp.Mesh(torch.from_numpy(w.coords).to(dev), w.d, w.dr, w.order) for w in ws]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    entries = [(m, torch.from_numpy(w.pts).to(dev), torch.from_numpy(w.field).to(dev)) for m, w in zip(meshes, ws)]
+    total = sum(e[1].shape[0] for e in entries)
+    res = {"workload": "64 meshes: quad2d/hex3d/sphere+torus surfaces, p=2..7, NE 1e3-5e4, 1e3-1e6 pts, nc=1",
+           "meshes": len(ws), "points": total, "elements": int(sum(w.NE for w in ws)),
+           "generate_s": gen_s, "setup_s": setup_s}
+    reps = max(3, args.steps // 2)
+
+    def timed(fn):
+        ms = []
+        for k in range(args.warmup + reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            b.synchronize()
+            if k >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        return statistics.mean(ms)
+
+    for prec, code_ in (("f64", fp.FP_F64), ("mixed", fp.FP_MIXED)):
+        b = fp.Batch(entries, code_)
+        t0 = time.perf_counter()
+        b.autotune()
+        tune_s = time.perf_counter() - t0
+        ms_batch = timed(b.run)
+        outs = b.outputs
+
+        def separate():
+            for (m, pts, fld), o in zip(entries, outs):
+                fp.fp_findpts(m.handle, pts, o[0], o[1], o[2], o[3])
+                fp.fp_eval(m.handle, o[0], o[1], o[2], fld, o[4].shape[0], o[4])
+
+        for m in meshes:
+            m.set_precision(code_)
+        ms_sep = timed(separate)
+        for m in meshes:
+            m.set_precision(fp.FP_F64)
+        res[prec] = {"value": total / (ms_batch / 1e3), "unit": "points/s", "ms_per_run": ms_batch,
+                     "separate_calls_ms": ms_sep, "speedup_vs_separate": ms_sep / ms_batch,
+                     "autotune_s": tune_s,
+                     "classes": [{"N": i.N, "d": i.d, "dr": i.dr, "items": i.n_items, "points": int(i.n_points),
+                                  "ctas_per_sm": i.ctas_per_sm, "chunk": i.chunk_points,
+                                  "ms": round(float(i.tuned_ms), 3)} for i in b.classes()]}
+        b.close()
+    res["speedup_mixed_vs_f64"] = res["mixed"]["value"] / res["f64"]["value"]
+    for m in meshes:
+        m.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,6 +290,7 @@ def main():
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-mixed", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -349,6 +413,7 @@ def main():
     status = mesh.device_status()
     mesh.close()
     mixed = None if args.skip_mixed else mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist)
+    batched = None if (args.skip_batch or rank != 0) else batch_block(fp, W, torch, dev, st, flush, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -373,7 +438,7 @@ def main():
                               "beta_iterations": int(sv[3]), "per_point_iterations": float(sv[1]) / n},
             "setup_ms": setup_ms, "wall_s_timed": wall, "device_status": status,
             "e2e": {"value": e2e_v, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "cpu_baseline": cpu, "clocks": clk, "mixed": mixed,
+            "cpu_baseline": cpu, "clocks": clk, "mixed": mixed, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

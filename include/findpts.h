@@ -151,6 +151,61 @@ int fp_findpts_mixed_noalloc(fp_mesh m, const double* pts_dev, int64_t n, int32_
 int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
             int64_t n, const double* field_dev, int nc, double* out, void* stream);
 
+/* ---- many meshes in one graph launch ---------------------------------------
+ * A batch plan runs find (and optionally eval) for many (mesh, point set)
+ * items at once: items are grouped by element shape (N, d, dr); per shape one
+ * persistent find launch covers every item's points (FP_F64, or FP_MIXED with
+ * its FP64 pass) and one launch interpolates the items that carry a field.
+ * The launches of all shapes are captured once into a CUDA graph on forked
+ * streams; fp_batch_run replays that graph.  Pointers are captured: the
+ * caller may change the point values between runs, not the buffers. */
+typedef struct {
+  int mesh;              /* index into the meshes array given to fp_batch_create */
+  const double* pts;     /* [n][d] device */
+  int64_t n;
+  int32_t* code;         /* outputs as fp_findpts, [n] / [n][dr], device */
+  int32_t* elem;
+  double* r;
+  double* dist2;
+  const double* field;   /* [nc][NE][N^dr] device, or NULL for no eval */
+  int nc;
+  double* out;           /* [nc][n] device (when field != NULL) */
+} fp_batch_item;
+
+typedef struct fp_batch_s* fp_batch;
+
+/* Builds the plan (item tables on the device, a scratch queue per shape for
+ * FP_MIXED) and captures the graph.  Launch shapes come from this process's
+ * earlier fp_batch_autotune results for the same shape, precision and point
+ * count (power-of-two bucket), else defaults.  Synchronous.
+ * Errors: FP_EINVAL (bad index, NULL buffer, n > 2^31-1), FP_ENOMEM,
+ * FP_ELAUNCH. */
+int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_item* items, int nitems,
+                    int precision, void* stream, fp_batch* out);
+
+/* Replays the captured graph on `stream` (asynchronous). */
+int fp_batch_run(fp_batch b, void* stream);
+
+/* The launch shape autotuner: for every element shape of the plan, times the
+ * shape's launches for CTAs per SM in {1, 2} and points per CTA chunk in
+ * {32, 128, 512} on the plan's own data (best of two timed runs each), keeps
+ * the fastest, records it for later plans and re-captures the graph.
+ * Overwrites the plan's outputs.  Synchronous. */
+int fp_batch_autotune(fp_batch b, void* stream);
+
+typedef struct {
+  int N, d, dr, n_items;
+  int64_t n_points;
+  int ctas_per_sm, chunk_points;
+  float tuned_ms; /* time of the chosen shape in the autotuner, -1 if untuned */
+} fp_batch_class_info;
+
+int fp_batch_num_classes(fp_batch b);
+int fp_batch_describe(fp_batch b, int i, fp_batch_class_info* info);
+
+/* Releases the plan (synchronises the device). */
+int fp_batch_free(fp_batch b);
+
 /* ---- introspection (tests, benchmarks) ----------------------------------- */
 typedef struct {
   int d, dr, N, M, n_grid;

@@ -190,6 +190,113 @@ def fp_alu_peak(which: int, iters: int = 4000, stream=None) -> float:
     return g.value
 
 
+class FpBatchItem(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_int), ("pts", _vp), ("n", ctypes.c_int64), ("code", _vp),
+                ("elem", _vp), ("r", _vp), ("dist2", _vp), ("field", _vp), ("nc", ctypes.c_int),
+                ("out", _vp)]
+
+
+class FpBatchClassInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("d", ctypes.c_int), ("dr", ctypes.c_int), ("n_items", ctypes.c_int),
+                ("n_points", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int), ("chunk_points", ctypes.c_int),
+                ("tuned_ms", ctypes.c_float)]
+
+
+def _batch_sig():
+    L = lib()
+    if getattr(L, "_batch_sig", False):
+        return L
+    L.fp_batch_create.argtypes = [ctypes.POINTER(_vp), _int, ctypes.POINTER(FpBatchItem), _int, _int, _vp,
+                                  ctypes.POINTER(_vp)]
+    L.fp_batch_run.argtypes = [_vp, _vp]
+    L.fp_batch_autotune.argtypes = [_vp, _vp]
+    L.fp_batch_free.argtypes = [_vp]
+    L.fp_batch_num_classes.argtypes = [_vp]
+    L.fp_batch_describe.argtypes = [_vp, _int, ctypes.POINTER(FpBatchClassInfo)]
+    for f in ("fp_batch_create", "fp_batch_run", "fp_batch_autotune", "fp_batch_free",
+              "fp_batch_num_classes", "fp_batch_describe"):
+        getattr(L, f).restype = _int
+    L._batch_sig = True
+    return L
+
+
+def fp_batch_create(meshes, items, precision: int = FP_F64, stream=None) -> _vp:
+    arr = (_vp * len(meshes))(*[m if isinstance(m, _vp) else _vp(m) for m in meshes])
+    its = (FpBatchItem * len(items))(*items)
+    h = _vp()
+    _check("fp_batch_create", _batch_sig().fp_batch_create(arr, len(meshes), its, len(items), int(precision),
+                                                           _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fp_batch_run(batch, stream=None) -> None:
+    _check("fp_batch_run", _batch_sig().fp_batch_run(batch, _stream(stream)))
+
+
+def fp_batch_autotune(batch, stream=None) -> None:
+    _check("fp_batch_autotune", _batch_sig().fp_batch_autotune(batch, _stream(stream)))
+
+
+def fp_batch_num_classes(batch) -> int:
+    return _batch_sig().fp_batch_num_classes(batch)
+
+
+def fp_batch_describe(batch, i: int) -> FpBatchClassInfo:
+    info = FpBatchClassInfo()
+    _check("fp_batch_describe", _batch_sig().fp_batch_describe(batch, int(i), ctypes.byref(info)))
+    return info
+
+
+def fp_batch_free(batch) -> None:
+    _check("fp_batch_free", _batch_sig().fp_batch_free(batch))
+
+
+class Batch:
+    """Find (+ eval) for many (Mesh, points[, field]) items in one graph
+    launch; allocates every item's outputs as torch tensors."""
+
+    def __init__(self, entries, precision: int = FP_F64, stream=None):
+        import torch
+        meshes, idx = [], {}
+        self.entries, self.outputs, items = entries, [], []
+        for mesh, pts, field in entries:
+            if id(mesh) not in idx:
+                idx[id(mesh)] = len(meshes)
+                meshes.append(mesh.handle)
+            n = pts.shape[0]
+            dev = pts.device
+            code = torch.empty(n, dtype=torch.int32, device=dev)
+            elem = torch.empty(n, dtype=torch.int32, device=dev)
+            r = torch.empty((n, mesh.dr), dtype=torch.float64, device=dev)
+            d2 = torch.empty(n, dtype=torch.float64, device=dev)
+            nc = 0 if field is None else field.numel() // (mesh.NE * mesh.N ** mesh.dr)
+            out = None if field is None else torch.empty((nc, n), dtype=torch.float64, device=dev)
+            self.outputs.append((code, elem, r, d2, out))
+            items.append(FpBatchItem(idx[id(mesh)], _ptr(pts, torch.float64, "pts"), n, _ptr(code), _ptr(elem),
+                                     _ptr(r), _ptr(d2), _ptr(field, torch.float64, "field"), nc, _ptr(out)))
+        self.handle = fp_batch_create(meshes, items, precision, stream)
+
+    def run(self, stream=None):
+        fp_batch_run(self.handle, stream)
+
+    def autotune(self, stream=None):
+        fp_batch_autotune(self.handle, stream)
+
+    def classes(self):
+        return [fp_batch_describe(self.handle, i) for i in range(fp_batch_num_classes(self.handle))]
+
+    def close(self):
+        if self.handle is not None:
+            fp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 FP_NOALLOC_MAX_POINTS = 1 << 20
 
 

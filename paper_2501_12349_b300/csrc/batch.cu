@@ -1,0 +1,358 @@
+// Batched find + eval over many meshes in one graph launch.
+//
+// A plan groups the caller's (mesh, points, outputs[, field]) items by
+// element shape (N, d, dr).  Per shape it uploads the item table once and
+// runs one persistent find launch over all its items (lanes pull points from
+// the whole shape's point sequence, so many small meshes fill the GPU
+// together), plus one eval launch.  The launches of all shapes are captured
+// once into a CUDA graph on forked streams; fp_batch_run replays it.  The
+// launch shape of each class (CTAs per SM, points per CTA chunk) is picked
+// by fp_batch_autotune, which times the candidates on the batch's own data.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "find_common.cuh"
+
+namespace fp {
+
+int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
+                       const BasisTab& B, int precision, int ctas_per_sm, int clog2, int* queue,
+                       int* qcount, unsigned long long* stats, cudaStream_t st);
+
+namespace {
+
+constexpr int kEvalThreads = 128;
+
+// Eval (Sec. 3.3) for every point of every item that carries a field.
+template <int N, int DR>
+__global__ void __launch_bounds__(kEvalThreads)
+    k_eval_batch(const BatchItem* __restrict__ items, int nitems, int64_t total, const BasisTab B) {
+  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].start <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchItem& it = items[lo];
+    if (it.field == nullptr || it.nc <= 0) continue;
+    const int64_t p = g - it.start;
+    const int c0 = it.code[p], e = it.elem[p];
+    const int64_t NE = it.m.NE;
+    if (c0 == FP_NOT_FOUND || e < 0 || e >= NE) {
+      if (c0 != FP_NOT_FOUND) record_status(it.m.status, FP_DEV_BAD_ELEM);
+      for (int c = 0; c < it.nc; ++c) it.out[(int64_t)c * it.n + p] = 0.0;
+      continue;
+    }
+    double ph[DR][N], dph[DR][N];
+#pragma unroll
+    for (int j = 0; j < DR; ++j) lagrange<N, double>(B.z, B.w, it.r[p * DR + j], ph[j], dph[j]);
+    for (int c = 0; c < it.nc; ++c) {
+      double v;
+      map_eval<N, DR, 1, false, double>(it.field + (c * NE + e) * NN, 0, ph, dph, &v, nullptr);
+      it.out[(int64_t)c * it.n + p] = v;
+    }
+  }
+}
+
+int launch_eval_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
+                      const BasisTab& B, cudaStream_t st) {
+  return dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+    constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
+    (void)Dc;
+    const int blocks = grid_for(total, kEvalThreads, sm_count() * 16);
+    k_eval_batch<NN, DR><<<blocks, kEvalThreads, 0, st>>>(items, nitems, total, B);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+  });
+}
+
+struct Tuning {
+  int ctas_per_sm = 2;
+  int clog2 = 5;
+  float ms = -1.f;  // measured time of the chosen shape, -1 if untuned
+};
+
+// Process-wide cache of tuned shapes: (N, d, dr, precision, log2 points).
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int>, Tuning> g_tune_cache;
+
+int log2_bucket(int64_t n) {
+  int b = 0;
+  while ((int64_t(1) << (b + 1)) <= n) ++b;
+  return b;
+}
+
+struct ClassPlan {
+  int N, d, dr;
+  BasisTab B;
+  std::vector<BatchItem> items;
+  int64_t total = 0;
+  BatchItem* d_items = nullptr;
+  int* d_queue = nullptr;  // total + 1 ints: mixed-path queue and its counter
+  bool has_field = false;
+  Tuning tune;
+  cudaStream_t side = nullptr;
+  cudaEvent_t join = nullptr;
+};
+
+}  // namespace
+}  // namespace fp
+
+struct fp_batch_s {
+  std::vector<fp::ClassPlan> classes;
+  int precision = FP_F64;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;  // the plan's own stream: the caller's may be
+                               // the legacy default stream, which cannot be captured
+  int64_t total_points = 0;
+};
+
+namespace fp {
+namespace {
+
+// Enqueues one class: counter reset, find launch(es), eval launch.
+int enqueue_class(ClassPlan& c, int precision, const Tuning& t, cudaStream_t st) {
+  if (c.total == 0) return FP_OK;
+  int* qcount = c.d_queue + c.total;
+  if (precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qcount, 0, sizeof(int), st));
+  FP_TRY(launch_batch_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, precision,
+                            t.ctas_per_sm, t.clog2, c.d_queue, qcount, nullptr, st));
+  if (c.has_field) FP_TRY(launch_eval_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, st));
+  return FP_OK;
+}
+
+void destroy_graph(fp_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Captures every class's work, each on its own forked stream, into b->exec.
+int capture(fp_batch_s* b) {
+  cudaStream_t st = b->cap;
+  destroy_graph(b);
+  FP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = FP_OK;
+  if (cudaEventRecord(b->fork, st) != cudaSuccess) rc = FP_ELAUNCH;
+  for (auto& c : b->classes) {
+    if (rc != FP_OK) break;
+    if (c.total == 0) continue;
+    if (cudaStreamWaitEvent(c.side, b->fork, 0) != cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+    rc = enqueue_class(c, b->precision, c.tune, c.side);
+    if (rc == FP_OK && (cudaEventRecord(c.join, c.side) != cudaSuccess ||
+                        cudaStreamWaitEvent(st, c.join, 0) != cudaSuccess))
+      rc = FP_ELAUNCH;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != FP_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != FP_OK ? rc : FP_ELAUNCH;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    destroy_graph(b);
+    return FP_ELAUNCH;
+  }
+  return FP_OK;
+}
+
+void free_plan(fp_batch_s* b) {
+  destroy_graph(b);
+  for (auto& c : b->classes) {
+    cudaFree(c.d_items);
+    cudaFree(c.d_queue);
+    if (c.side) cudaStreamDestroy(c.side);
+    if (c.join) cudaEventDestroy(c.join);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+}  // namespace
+}  // namespace fp
+
+extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_item* items,
+                               int nitems, int precision, void* stream, fp_batch* out) {
+  using namespace fp;
+  if (!out) return FP_EINVAL;
+  *out = nullptr;
+  if (!meshes || nm <= 0 || !items || nitems <= 0) return FP_EINVAL;
+  if (precision != FP_F64 && precision != FP_MIXED) return FP_EINVAL;
+  for (int i = 0; i < nitems; ++i) {
+    const fp_batch_item& it = items[i];
+    if (it.mesh < 0 || it.mesh >= nm || !meshes[it.mesh] || it.n < 0 || it.n > INT32_MAX) return FP_EINVAL;
+    if (it.n > 0 && (!it.pts || !it.code || !it.elem || !it.r || !it.dist2)) return FP_EINVAL;
+    if (it.field && (it.nc <= 0 || !it.out)) return FP_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  fp_batch_s* b = new fp_batch_s();
+  b->precision = precision;
+  // group by element shape, items kept in the caller's order within a class
+  std::map<std::tuple<int, int, int>, int> cls;
+  for (int i = 0; i < nitems; ++i) {
+    const fp_mesh_s* m = meshes[items[i].mesh];
+    const auto key = std::make_tuple(m->N, m->d, m->dr);
+    auto f = cls.find(key);
+    int ci;
+    if (f == cls.end()) {
+      ci = (int)b->classes.size();
+      cls[key] = ci;
+      b->classes.emplace_back();
+      ClassPlan& c = b->classes.back();
+      c.N = m->N;
+      c.d = m->d;
+      c.dr = m->dr;
+      c.B = m->basis;
+    } else {
+      ci = f->second;
+    }
+    ClassPlan& c = b->classes[ci];
+    BatchItem bi;
+    memset(&bi, 0, sizeof(bi));
+    bi.m = m->view();
+    bi.pts = items[i].pts;
+    bi.n = items[i].n;
+    bi.start = c.total;
+    bi.code = items[i].code;
+    bi.elem = items[i].elem;
+    bi.r = items[i].r;
+    bi.dist2 = items[i].dist2;
+    bi.field = items[i].field;
+    bi.nc = items[i].field ? items[i].nc : 0;
+    bi.out = items[i].out;
+    if (bi.field) c.has_field = true;
+    if (bi.n > 0) {
+      c.items.push_back(bi);
+      c.total += bi.n;
+    }
+  }
+  int rc = FP_OK;
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    rc = FP_ELAUNCH;
+  for (auto& c : b->classes) {
+    if (rc != FP_OK) break;
+    b->total_points += c.total;
+    if (c.total > INT32_MAX) {
+      rc = FP_EINVAL;
+      break;
+    }
+    if (c.items.empty()) continue;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto f = g_tune_cache.find(std::make_tuple(c.N, c.d, c.dr, precision, log2_bucket(c.total)));
+      if (f != g_tune_cache.end()) c.tune = f->second;
+    }
+    if (cudaMalloc(&c.d_items, sizeof(BatchItem) * c.items.size()) != cudaSuccess ||
+        cudaMalloc(&c.d_queue, sizeof(int) * (size_t)(c.total + 1)) != cudaSuccess) {
+      rc = FP_ENOMEM;
+      break;
+    }
+    if (cudaMemcpyAsync(c.d_items, c.items.data(), sizeof(BatchItem) * c.items.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming) != cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+  }
+  if (rc == FP_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = FP_ELAUNCH;
+  if (rc == FP_OK) rc = capture(b);
+  if (rc != FP_OK) {
+    cudaStreamSynchronize(st);
+    free_plan(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return FP_OK;
+}
+
+extern "C" int fp_batch_run(fp_batch b, void* stream) {
+  if (!b || !b->exec) return FP_EINVAL;
+  FP_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+  return FP_OK;
+}
+
+extern "C" int fp_batch_autotune(fp_batch b, void* stream) {
+  using namespace fp;
+  if (!b) return FP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ctas[2] = {1, 2};
+  const int clogs[3] = {5, 7, 9};
+  cudaEvent_t e0, e1;
+  FP_CUDA_TRY(cudaEventCreate(&e0));
+  FP_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = FP_OK;
+  for (auto& c : b->classes) {
+    if (c.total == 0 || rc != FP_OK) continue;
+    Tuning best;
+    for (int a = 0; a < 2 && rc == FP_OK; ++a)
+      for (int k = 0; k < 3 && rc == FP_OK; ++k) {
+        Tuning t;
+        t.ctas_per_sm = ctas[a];
+        t.clog2 = clogs[k];
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3 && rc == FP_OK; ++rep) {  // first rep warms up
+          cudaEventRecord(e0, st);
+          rc = enqueue_class(c, b->precision, t, st);
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) rc = FP_ELAUNCH;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) ms_best = std::min(ms_best, ms);
+        }
+        t.ms = ms_best;
+        if (best.ms < 0.f || t.ms < best.ms) best = t;
+      }
+    if (rc == FP_OK) {
+      c.tune = best;
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_cache[std::make_tuple(c.N, c.d, c.dr, b->precision, log2_bucket(c.total))] = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == FP_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = FP_ELAUNCH;
+  if (rc == FP_OK) rc = capture(b);
+  return rc;
+}
+
+extern "C" int fp_batch_describe(fp_batch b, int i, fp_batch_class_info* info) {
+  if (!b || !info || i < 0 || i >= (int)b->classes.size()) return FP_EINVAL;
+  const auto& c = b->classes[i];
+  info->N = c.N;
+  info->d = c.d;
+  info->dr = c.dr;
+  info->n_items = (int)c.items.size();
+  info->n_points = c.total;
+  info->ctas_per_sm = c.tune.ctas_per_sm;
+  info->chunk_points = 1 << c.tune.clog2;
+  info->tuned_ms = c.tune.ms;
+  return FP_OK;
+}
+
+extern "C" int fp_batch_num_classes(fp_batch b) { return b ? (int)b->classes.size() : FP_EINVAL; }
+
+extern "C" int fp_batch_free(fp_batch b) {
+  if (!b) return FP_EINVAL;
+  cudaDeviceSynchronize();
+  fp::free_plan(b);
+  delete b;
+  return FP_OK;
+}

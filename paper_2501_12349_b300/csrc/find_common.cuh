@@ -457,6 +457,87 @@ __device__ __forceinline__ bool trial_accepts(T F, T Fn, T pred, bool clipped, T
   return false;
 }
 
+// ---- sources of work: one mesh, or a batch of (mesh, points) items ---------
+
+// One mesh; the point sequence is pts[0..n) or pts[pidx[0..n)].  The
+// "global" index of a point (what the mixed path queues) is its index.
+template <int D, int DR>
+struct SingleWork {
+  const DevMesh* mesh;
+  const double* pts;
+  const int* pidx;
+  int64_t n;
+  int* code;
+  int* elem;
+  double* r;
+  double* dist2;
+  int clog2;  // a CTA takes 2^clog2 consecutive points per chunk
+  __device__ __forceinline__ const DevMesh* first() const { return mesh; }
+  __device__ __forceinline__ void locate(int64_t g, const DevMesh*& m, int& item, int64_t& p) const {
+    m = mesh;
+    item = 0;
+    p = pidx ? (int64_t)__ldg(pidx + g) : g;
+  }
+  __device__ __forceinline__ void load(int, int64_t p, double (&xs)[D]) const {
+#pragma unroll
+    for (int c = 0; c < D; ++c) xs[c] = __ldg(pts + p * D + c);
+  }
+  __device__ __forceinline__ void write(int, int64_t p, int c, int e, const double (&rr)[DR], double d2) const {
+    write_result<DR>(p, c, e, rr, d2, code, elem, r, dist2);
+  }
+  __device__ __forceinline__ int64_t global(int, int64_t p) const { return p; }
+};
+
+// One (mesh, points, outputs) item of a batch; `start` is the index of its
+// first point in the batch's global point sequence (items in order).
+struct BatchItem {
+  DevMesh m;
+  const double* pts;
+  int64_t n;
+  int64_t start;
+  int* code;
+  int* elem;
+  double* r;
+  double* dist2;
+  const double* field;
+  int nc;
+  double* out;
+};
+
+// A batch of items of one element shape; the point sequence is the items'
+// points in order, or the global indices gidx[0..n).
+template <int D, int DR>
+struct BatchWork {
+  const BatchItem* items;
+  int nitems;
+  const int* gidx;
+  int64_t n;
+  int clog2;
+  __device__ __forceinline__ const DevMesh* first() const { return &items[0].m; }
+  __device__ __forceinline__ void locate(int64_t g, const DevMesh*& m, int& item, int64_t& p) const {
+    const int64_t gg = gidx ? (int64_t)__ldg(gidx + g) : g;
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {  // last item with start <= gg
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].start <= gg) lo = mid;
+      else hi = mid - 1;
+    }
+    item = lo;
+    m = &items[lo].m;
+    p = gg - items[lo].start;
+  }
+  __device__ __forceinline__ void load(int item, int64_t p, double (&xs)[D]) const {
+    const double* pts = items[item].pts;
+#pragma unroll
+    for (int c = 0; c < D; ++c) xs[c] = __ldg(pts + p * D + c);
+  }
+  __device__ __forceinline__ void write(int item, int64_t p, int c, int e, const double (&rr)[DR], double d2) const {
+    const BatchItem& it = items[item];
+    write_result<DR>(p, c, e, rr, d2, it.code, it.elem, it.r, it.dist2);
+  }
+  __device__ __forceinline__ int64_t global(int item, int64_t p) const { return items[item].start + p; }
+};
+
 int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
              int* elem, double* r, double* dist2, unsigned long long* stats, cudaStream_t st);
 int find_mixed(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem, double* r,

@@ -22,13 +22,10 @@ namespace fp {
 enum : int { M_IDLE = 0, M_SCAN = 1, M_NEWTON = 2, M_RESTORE = 3, M_DONE = 4 };
 enum : int { E_INIT = 1, E_TRIAL = 2, E_RESTORE = 3 };
 
-template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, 2)
-    k_find_f64(const DevMesh m, const BasisTab B, const double* __restrict__ pts,
-               const int* __restrict__ pidx, int64_t n, const int* __restrict__ n_dev,
-               int* __restrict__ code,
-               int* __restrict__ elem, double* __restrict__ rout, double* __restrict__ dist2,
-               unsigned long long* stats) {
+// The FP64 lane loop over a source of work (SingleWork or BatchWork); all
+// meshes of one launch share N, D, DR and so the basis table B.
+template <int N, int D, int DR, class Work>
+__device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, unsigned long long* stats) {
   constexpr int NN = (DR == 3) ? N * N * N : N * N;
   __shared__ double s_slab[DR == 3 ? 3 * N * kFindThreads : 1];
   const TSlots<N, double> ts{s_slab};
@@ -36,8 +33,11 @@ __global__ void __launch_bounds__(kFindThreads, 2)
   if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
   Counters cnt;
-  if (n_dev) n = *n_dev;  // a queue length produced on the device
-  const int64_t nchunks = (n + 31) / 32;
+  const int64_t n = w.n;
+  const int clog2 = w.clog2;
+  const int64_t nchunks = (n + (1 << clog2) - 1) >> clog2;
+  const DevMesh* mp = w.first();
+  int item = 0;
   int mode = M_IDLE, etype = E_INIT;
   int64_t pi = 0;
   double xs[D];
@@ -57,51 +57,49 @@ __global__ void __launch_bounds__(kFindThreads, 2)
     // ---- per-lane bookkeeping until this lane needs one evaluation --------
     while (mode != M_DONE && !need) {
       if (++guard > (1u << 26)) {
-        record_status(m.status, FP_DEV_SPIN_CAP);
+        record_status(mp->status, FP_DEV_SPIN_CAP);
         mode = M_DONE;
         break;
       }
       if (mode == M_IDLE) {
         const unsigned long long s = atomicAdd(&s_next, 1ull);
-        const int64_t chunk = (int64_t)(s >> 5) * gridDim.x + blockIdx.x;
+        const int64_t chunk = (int64_t)(s >> clog2) * gridDim.x + blockIdx.x;
         if (chunk >= nchunks) {
           mode = M_DONE;
           break;
         }
-        const int64_t p = chunk * 32 + (int64_t)(s & 31);
-        if (p >= n) continue;
-        pi = pidx ? (int64_t)__ldg(pidx + p) : p;
+        const int64_t g = (chunk << clog2) + (int64_t)(s & ((1u << clog2) - 1));
+        if (g >= n) continue;
+        w.locate(g, mp, item, pi);
+        w.load(item, pi, xs);
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          xs[c] = __ldg(pts + pi * D + c);
-          x32[c] = (float)xs[c];
-        }
+        for (int c = 0; c < D; ++c) x32[c] = (float)xs[c];
         bcode = FP_NOT_FOUND;
         be = -1;
         bd = INFINITY;
 #pragma unroll
         for (int j = 0; j < DR; ++j) br[j] = 0.0;
-        const int64_t cell = point_cell<D>(m, xs);
+        const int64_t cell = point_cell<D>(*mp, xs);
         if (cell < 0) {
-          write_result<DR>(pi, bcode, be, br, bd, code, elem, rout, dist2);
+          w.write(item, pi, bcode, be, br, bd);
           continue;
         }
-        q = __ldg(m.cell_start + cell);
-        qend = __ldg(m.cell_start + cell + 1);
+        q = __ldg(mp->cell_start + cell);
+        qend = __ldg(mp->cell_start + cell + 1);
         mode = M_SCAN;
       }
       if (mode == M_SCAN) {
-        e = next_candidate<D>(m, xs, x32, q, qend, cnt);
+        e = next_candidate<D>(*mp, xs, x32, q, qend, cnt);
         if (e < 0) {
-          write_result<DR>(pi, bcode, be, br, bd, code, elem, rout, dist2);
+          w.write(item, pi, bcode, be, br, bd);
           mode = M_IDLE;
           continue;
         }
         ++cnt.v[0];
-        xscale = aabb_scale<D>(m, e);
+        xscale = aabb_scale<D>(*mp, e);
         float xr[D];
-        rel_point<D>(m, e, xs, xr);
-        const int nb = closest_node<N, D, DR>(m, e, xs, xr);
+        rel_point<D>(*mp, e, xs, xr);
+        const int nb = closest_node<N, D, DR>(*mp, e, xs, xr);
         node_coords<N, DR>(B, nb, r);
         etype = E_INIT;
         need = true;
@@ -114,18 +112,18 @@ __global__ void __launch_bounds__(kFindThreads, 2)
       }
       // mode == M_NEWTON: one step of Sec. 3.2.1 from (r, dx, G, F, alpha)
       bool done = false;
-      if (l >= m.max_iter) {
+      if (l >= mp->max_iter) {
         done = true;
       } else {
         const bool beta = (l > 0) && at_bound<DR>(r);
         double HS[DR][DR];
         if (beta) {
-          hess_term<N, D, DR, double>(m.coords + (int64_t)e * NN, m.cstride, B, r, dx, ts, HS);
+          hess_term<N, D, DR, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r, dx, ts, HS);
         }
         double ds[DR];
         bool used_beta;
         const double mx = newton_step<D, DR>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
-        if (mx < m.newton_tol) {
+        if (mx < mp->newton_tol) {
           // the last step is taken; dist2 from the linear model at r
           F = model_dist2<D, DR>(G, dx, ds);
 #pragma unroll
@@ -148,7 +146,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
         bool inside = true;
 #pragma unroll
         for (int j = 0; j < DR; ++j) inside &= fabs(r[j]) < 1.0;
-        if (DR < D) inside &= F < m.dist_tol;
+        if (DR < D) inside &= F < mp->dist_tol;
         if (inside || F < bd) {
           bcode = inside ? FP_INTERIOR : FP_BORDER;
           be = e;
@@ -157,7 +155,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
           for (int j = 0; j < DR; ++j) br[j] = r[j];
         }
         if (inside) {
-          write_result<DR>(pi, bcode, be, br, bd, code, elem, rout, dist2);
+          w.write(item, pi, bcode, be, br, bd);
           mode = M_IDLE;
         } else {
           mode = M_SCAN;
@@ -171,7 +169,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
 #pragma unroll
       for (int j = 0; j < DR; ++j) re[j] = (etype == E_TRIAL) ? rn[j] : r[j];
       double xv[D];
-      eval_xG<N, D, DR, true, double>(m.coords + (int64_t)e * NN, m.cstride, B, re, ts, xv, G);
+      eval_xG<N, D, DR, true, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, re, ts, xv, G);
       double Fn = 0.0;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
@@ -200,6 +198,27 @@ __global__ void __launch_bounds__(kFindThreads, 2)
     }
   }
   cnt.flush(stats);
+}
+
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kFindThreads, 2)
+    k_find_f64(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
+               const int* __restrict__ pidx, int64_t n, const int* __restrict__ n_dev,
+               int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
+               double* __restrict__ dist2, unsigned long long* stats) {
+  const SingleWork<D, DR> w{&m, pts, pidx, n_dev ? (int64_t)*n_dev : n, code, elem, rout, dist2, 5};
+  find_f64_loop<N, D, DR>(w, B, stats);
+}
+
+// Every item of a batch (one element shape) in one persistent launch; gidx /
+// n_dev optionally restrict it to a device-produced list of global indices.
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kFindThreads, 2)
+    k_find_f64_batch(const BatchItem* __restrict__ items, int nitems, int64_t total,
+                     const int* __restrict__ gidx, const int* __restrict__ n_dev, const BasisTab B,
+                     int clog2, unsigned long long* stats) {
+  const BatchWork<D, DR> w{items, nitems, gidx, n_dev ? (int64_t)*n_dev : total, clog2};
+  find_f64_loop<N, D, DR>(w, B, stats);
 }
 
 }  // namespace fp

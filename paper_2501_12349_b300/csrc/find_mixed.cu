@@ -36,12 +36,10 @@ constexpr float kBorder32 = 1e-4f; // "clearly outside": distance > kBorder32 * 
 constexpr int kPark = 28;          // run the FP64 refinement with >= kPark lanes parked
 constexpr int kMaxRefine = 4;
 
-template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, 2)
-    k_find_mixed(const DevMesh m, const BasisTab B, const double* __restrict__ pts, int64_t n,
-                 int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
-                 double* __restrict__ dist2, int* __restrict__ queue, int* __restrict__ qcount,
-                 unsigned long long* stats) {
+// The mixed-precision lane loop over a source of work (see find_f64.cuh).
+template <int N, int D, int DR, class Work>
+__device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B, int* __restrict__ queue,
+                                                int* __restrict__ qcount, unsigned long long* stats) {
   constexpr int NN = (DR == 3) ? N * N * N : N * N;
   __shared__ double s_slab64[DR == 3 ? 2 * N * kFindThreads : 1];
   __shared__ float s_slab32[DR == 3 ? 3 * N * kFindThreads : 1];
@@ -51,7 +49,11 @@ __global__ void __launch_bounds__(kFindThreads, 2)
   if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
   Counters cnt;
-  const int64_t nchunks = (n + 31) / 32;
+  const int64_t n = w.n;
+  const int clog2 = w.clog2;
+  const int64_t nchunks = (n + (1 << clog2) - 1) >> clog2;
+  const DevMesh* mp = w.first();
+  int item = 0;
   int mode = X_IDLE, etype = X_INIT;
   int64_t pi = 0;
   double xs[D];
@@ -69,54 +71,53 @@ __global__ void __launch_bounds__(kFindThreads, 2)
     bool need = false;
     while (mode != X_DONE && mode != X_PARK && !need) {
       if (++guard > (1u << 26)) {
-        record_status(m.status, FP_DEV_SPIN_CAP);
+        record_status(mp->status, FP_DEV_SPIN_CAP);
         mode = X_DONE;
         break;
       }
       if (mode == X_IDLE) {
         const unsigned long long s = atomicAdd(&s_next, 1ull);
-        const int64_t chunk = (int64_t)(s >> 5) * gridDim.x + blockIdx.x;
+        const int64_t chunk = (int64_t)(s >> clog2) * gridDim.x + blockIdx.x;
         if (chunk >= nchunks) {
           mode = X_DONE;
           break;
         }
-        pi = chunk * 32 + (int64_t)(s & 31);
-        if (pi >= n) continue;
+        const int64_t g = (chunk << clog2) + (int64_t)(s & ((1u << clog2) - 1));
+        if (g >= n) continue;
+        w.locate(g, mp, item, pi);
+        w.load(item, pi, xs);
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          xs[c] = __ldg(pts + pi * D + c);
-          x32[c] = (float)xs[c];
-        }
+        for (int c = 0; c < D; ++c) x32[c] = (float)xs[c];
         has_border = false;
-        const int64_t cell = point_cell<D>(m, xs);
+        const int64_t cell = point_cell<D>(*mp, xs);
         if (cell < 0) {
           const double z0[DR] = {};
-          write_result<DR>(pi, FP_NOT_FOUND, -1, z0, INFINITY, code, elem, rout, dist2);
+          w.write(item, pi, FP_NOT_FOUND, -1, z0, INFINITY);
           continue;
         }
-        q = __ldg(m.cell_start + cell);
-        qend = __ldg(m.cell_start + cell + 1);
+        q = __ldg(mp->cell_start + cell);
+        qend = __ldg(mp->cell_start + cell + 1);
         mode = X_SCAN;
       }
       if (mode == X_SCAN) {
-        e = next_candidate<D>(m, xs, x32, q, qend, cnt);
+        e = next_candidate<D>(*mp, xs, x32, q, qend, cnt);
         if (e < 0) {
           if (has_border) {
-            queue[atomicAdd(qcount, 1)] = (int)pi;
+            queue[atomicAdd(qcount, 1)] = (int)w.global(item, pi);
             ++cnt.v[6];
           } else {
             const double z0[DR] = {};
-            write_result<DR>(pi, FP_NOT_FOUND, -1, z0, INFINITY, code, elem, rout, dist2);
+            w.write(item, pi, FP_NOT_FOUND, -1, z0, INFINITY);
           }
           mode = X_IDLE;
           continue;
         }
         ++cnt.v[0];
-        rel_point<D>(m, e, xs, xr);
-        xrel = __ldg(m.box32 + (int64_t)e * BOX32 + 18);
+        rel_point<D>(*mp, e, xs, xr);
+        xrel = __ldg(mp->box32 + (int64_t)e * BOX32 + 18);
         // closest node in FP32 (the start only changes the path, not the
         // converged result, and FP64 decides everything that matters)
-        const float* X32 = m.coords32 + (int64_t)e * NN;
+        const float* X32 = mp->coords32 + (int64_t)e * NN;
         float b1 = INFINITY;
         int nb = 0;
 #pragma unroll 4
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
           float d = 0.f;
 #pragma unroll
           for (int c = 0; c < D; ++c) {
-            const float t = xr[c] - __ldg(X32 + c * m.cstride + nn);
+            const float t = xr[c] - __ldg(X32 + c * mp->cstride + nn);
             d = fmaf(t, t, d);
           }
           if (d < b1) {
@@ -144,12 +145,12 @@ __global__ void __launch_bounds__(kFindThreads, 2)
       }
       // X_NEWTON: one FP32 step
       bool done = false, converged = false;
-      if (l >= m.max_iter) {
+      if (l >= mp->max_iter) {
         done = true;
       } else {
         const bool beta = (l > 0) && at_bound<DR>(r);
         float HS[DR][DR];
-        if (beta) hess_term<N, D, DR, float>(m.coords32 + (int64_t)e * NN, m.cstride, B, r, dx, ts32, HS);
+        if (beta) hess_term<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, ts32, HS);
         float ds[DR];
         bool used_beta;
         const float mx = newton_step<D, DR, float>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
 #pragma unroll
         for (int j = 0; j < DR; ++j) inside &= fabsf(r[j]) < 1.f;
         const float far2 = (kBorder32 * xrel) * (kBorder32 * xrel);
-        const float dtol = (float)m.dist_tol;
+        const float dtol = (float)mp->dist_tol;
         if (converged && inside && (DR == D || F < 0.5f * dtol)) {
 #pragma unroll
           for (int j = 0; j < DR; ++j) r64[j] = (double)r[j];
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
           has_border = true;
           mode = X_SCAN;
         } else {
-          queue[atomicAdd(qcount, 1)] = (int)pi;
+          queue[atomicAdd(qcount, 1)] = (int)w.global(item, pi);
           ++cnt.v[6];
           mode = X_IDLE;
         }
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
     if ((__popc(parked) >= kPark || busy == 0) && mode == X_PARK) {
       ++cnt.v[4];
       double xv[D], dxd[D], Gd[D * DR];
-      eval_xG<N, D, DR, false, double>(m.coords + (int64_t)e * NN, m.cstride, B, r64, ts64, xv, nullptr);
+      eval_xG<N, D, DR, false, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r64, ts64, xv, nullptr);
 #pragma unroll
       for (int c = 0; c < D; ++c) dxd[c] = xs[c] - xv[c];
 #pragma unroll
@@ -240,10 +241,10 @@ __global__ void __launch_bounds__(kFindThreads, 2)
         mx = fmax(mx, fabs(s[j]));
       }
       if (!inside) {
-        queue[atomicAdd(qcount, 1)] = (int)pi;
+        queue[atomicAdd(qcount, 1)] = (int)w.global(item, pi);
         ++cnt.v[6];
         mode = X_IDLE;
-      } else if (mx < m.newton_tol) {
+      } else if (mx < mp->newton_tol) {
         double f = 0.0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -252,15 +253,15 @@ __global__ void __launch_bounds__(kFindThreads, 2)
           for (int j = 0; j < DR; ++j) t -= Gd[c * DR + j] * s[j];
           f += t * t;
         }
-        if (DR < D && !(f < m.dist_tol)) {
-          queue[atomicAdd(qcount, 1)] = (int)pi;
+        if (DR < D && !(f < mp->dist_tol)) {
+          queue[atomicAdd(qcount, 1)] = (int)w.global(item, pi);
           ++cnt.v[6];
         } else {
-          write_result<DR>(pi, FP_INTERIOR, e, rnn, f, code, elem, rout, dist2);
+          w.write(item, pi, FP_INTERIOR, e, rnn, f);
         }
         mode = X_IDLE;
       } else if (++nref >= kMaxRefine) {
-        queue[atomicAdd(qcount, 1)] = (int)pi;
+        queue[atomicAdd(qcount, 1)] = (int)w.global(item, pi);
         ++cnt.v[6];
         mode = X_IDLE;
       } else {
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
 #pragma unroll
       for (int j = 0; j < DR; ++j) re[j] = (etype == X_TRIAL) ? rn[j] : r[j];
       float xv[D];
-      eval_xG<N, D, DR, true, float>(m.coords32 + (int64_t)e * NN, m.cstride, B, re, ts32, xv, G);
+      eval_xG<N, D, DR, true, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, re, ts32, xv, G);
       float Fn = 0.f;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
@@ -303,6 +304,25 @@ __global__ void __launch_bounds__(kFindThreads, 2)
     }
   }
   cnt.flush(stats);
+}
+
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kFindThreads, 2)
+    k_find_mixed(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
+                 int64_t n, int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
+                 double* __restrict__ dist2, int* __restrict__ queue, int* __restrict__ qcount,
+                 unsigned long long* stats) {
+  const SingleWork<D, DR> w{&m, pts, nullptr, n, code, elem, rout, dist2, 5};
+  find_mixed_loop<N, D, DR>(w, B, queue, qcount, stats);
+}
+
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kFindThreads, 2)
+    k_find_mixed_batch(const BatchItem* __restrict__ items, int nitems, int64_t total, const BasisTab B,
+                       int* __restrict__ queue, int* __restrict__ qcount, int clog2,
+                       unsigned long long* stats) {
+  const BatchWork<D, DR> w{items, nitems, nullptr, total, clog2};
+  find_mixed_loop<N, D, DR>(w, B, queue, qcount, stats);
 }
 
 }  // namespace
@@ -346,6 +366,31 @@ int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, int64_t n, in
                                                             queue, qcount, stats);
     k_find_f64<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount, code,
                                                           elem, r, dist2, stats);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+  });
+}
+
+}  // namespace fp
+
+namespace fp {
+
+// One element shape of a batch: the mixed kernel over all items, then the
+// FP64 kernel over the queued global indices (queue capacity >= total).
+int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
+                       const BasisTab& B, int precision, int ctas_per_sm, int clog2, int* queue,
+                       int* qcount, unsigned long long* stats, cudaStream_t st) {
+  return dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+    constexpr int NN = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
+    const int blocks = persistent_blocks(total, ctas_per_sm);
+    if (precision == FP_MIXED) {
+      k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, B, queue, qcount,
+                                                                     clog2, stats);
+      k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, queue, qcount, B,
+                                                                   clog2, stats);
+    } else {
+      k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, nullptr, nullptr, B,
+                                                                   clog2, stats);
+    }
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
   });
 }

@@ -176,6 +176,22 @@ def outside_unit_box_points(rng, n: int, d: int, lo: float = -0.1, hi: float = 1
     return out[:n]
 
 
+def analytic_surface_points(rng, name: str, n: int, offset: np.ndarray) -> np.ndarray:
+    """Points on the analytic sphere (radius 1) or torus (R = 1, r = 0.3)
+    that the cubed-sphere / torus meshes interpolate, displaced by `offset`
+    along the analytic normal (physical-space inputs for benchmarks; the
+    interpolated surface differs from the analytic one by the interpolation
+    error, so on-surface points end INTERIOR or BORDER by that error)."""
+    if "sphere" in name:
+        v = rng.normal(size=(n, 3))
+        v /= np.linalg.norm(v, axis=1)[:, None]
+        return v * (1.0 + offset)[:, None]
+    u = rng.uniform(0, 2 * np.pi, n)
+    t = rng.uniform(0, 2 * np.pi, n)
+    rr = 0.3 + offset
+    return np.stack([(1.0 + rr * np.cos(t)) * np.cos(u), (1.0 + rr * np.cos(t)) * np.sin(u), rr * np.sin(t)], 1)
+
+
 def element_reference_points(rng, n: int, NE: int, dr: int, rmax: float = 0.95):
     """(elem, r) pairs: elem uniform in [0, NE), r uniform in [-rmax, rmax]^dr."""
     elem = rng.integers(0, NE, size=n).astype(np.int32)
@@ -296,6 +312,7 @@ def config4(seed: int = 4, max_points: int | None = None, max_elems: int | None 
             elem, r = element_reference_points(rng, npts, NE, 2, rmax=1.0)
             off = np.where(rng.uniform(size=npts) < 0.01, 0.1 * h, 0.0)
             w = Workload(name, coords, 3, 2, p, None, fwd_elem=elem, fwd_r=r, fwd_offset=off, h=h)
+            w.pts = analytic_surface_points(rng, name, npts, off)
         w.field, _ = polynomial_field(w.coords, rng, min(p, 3))
         out.append(w)
     return out
