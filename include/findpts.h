@@ -56,6 +56,7 @@ extern "C" {
 #define FP_ETIMEDOUT (-5)    /* a host-side wait ran out                      */
 #define FP_EBUSY (-6)        /* resource in use                               */
 #define FP_EUNSUPPORTED (-7) /* element type / order not built               */
+#define FP_ECANCELED (-8)    /* a server request was cancelled               */
 
 /* ---- per-point location codes (Sec. 3.2, the enum c*) ------------------- */
 #define FP_INTERIOR 0
@@ -205,6 +206,80 @@ int fp_batch_describe(fp_batch b, int i, fp_batch_class_info* info);
 
 /* Releases the plan (synchronises the device). */
 int fp_batch_free(fp_batch b);
+
+/* ---- continuous-batching server -------------------------------------------
+ * Meshes (and their fields) stay resident; requests are submitted from any
+ * host thread and run as soon as a slot and device memory are free:
+ *   FP_REQ_REMAP    find the points, interpolate the mesh's remap field
+ *                   (Find once + Interpolate, Secs. 3.2-3.3; the remap use of
+ *                   Sec. 6.4);
+ *   FP_REQ_PARTICLE rk_steps explicit-midpoint steps of size dt through the
+ *                   mesh's velocity field (Find / Interpolate / Integrate, the
+ *                   particle-tracking loop of Sec. 6.7), then a final find of
+ *                   the end positions; a particle that leaves the mesh is
+ *                   NOT_FOUND and stops.
+ * A scheduler thread packs one stage of every ready request into each tick
+ * (batched launches across requests, grouped by element shape; up to two
+ * ticks in flight), so requests that arrive while others run are admitted
+ * and overlap on the device.  A request's result does not depend on what
+ * else is in flight. */
+#define FP_REQ_REMAP 0
+#define FP_REQ_PARTICLE 1
+
+typedef struct fp_server_s* fp_server;
+
+typedef struct {
+  size_t mem_budget;     /* device bytes for request buffers (admission)      */
+  int max_active;        /* requests admitted at once (slots)                  */
+  int precision;         /* FP_F64 or FP_MIXED                                 */
+  double tick_timeout_s; /* host watchdog per tick: its requests fail with     */
+                         /* FP_ETIMEDOUT (memory kept until the tick ends)     */
+} fp_server_opts;
+
+typedef struct {
+  int64_t submitted, admitted, completed, cancelled, ticks, timeouts;
+  int64_t active, queued;
+  size_t bytes_in_use;
+} fp_server_stats;
+
+void fp_server_opts_default(fp_server_opts* opts); /* 1 GiB, 64 slots, FP_MIXED, 30 s */
+
+/* remap_fields[i] ([nc_remap[i]][NE][N^dr], device) and velocity[i]
+ * ([d][NE][N^dr], device) may be NULL (arrays themselves may be NULL); they
+ * must stay valid until fp_server_destroy.  Starts the scheduler thread. */
+int fp_server_create(const fp_mesh* meshes, int nm, const double* const* remap_fields,
+                     const int* nc_remap, const double* const* velocity,
+                     const fp_server_opts* opts, fp_server* out);
+
+/* Queues a request.  Host buffers (pinned memory recommended) must stay
+ * valid until the request is done; outputs:
+ *   code_host[n], elem_host[n], r_host[n][dr], dist2_host[n] (any may be
+ *   NULL), out_host = remap: interpolated values [nc][n]; particle: final
+ *   positions [n][d].
+ * Errors: FP_EINVAL; FP_ENOMEM if the request could never fit the budget. */
+int fp_server_submit(fp_server s, int mesh, int kind, const double* pts_host, int64_t n,
+                     int rk_steps, double dt, int32_t* code_host, int32_t* elem_host,
+                     double* r_host, double* dist2_host, double* out_host, int64_t* req_id);
+
+/* Never blocks on the device: *done = 1 when finished (*status its result). */
+int fp_server_poll(fp_server s, int64_t req_id, int* done, int* status);
+
+/* Blocks up to timeout_s: the request's status, or FP_ETIMEDOUT. */
+int fp_server_wait(fp_server s, int64_t req_id, double timeout_s);
+
+/* Cancels a request not yet admitted (FP_EBUSY otherwise). */
+int fp_server_cancel(fp_server s, int64_t req_id);
+
+/* Seconds from submission to admission and to completion (done requests). */
+int fp_server_timing(fp_server s, int64_t req_id, double* queued_s, double* total_s);
+
+/* Forgets a finished request (its id becomes invalid). */
+int fp_server_release(fp_server s, int64_t req_id);
+
+int fp_server_get_stats(fp_server s, fp_server_stats* stats);
+
+/* Stops the scheduler, waits for the device, frees everything. */
+int fp_server_destroy(fp_server s);
 
 /* ---- introspection (tests, benchmarks) ----------------------------------- */
 typedef struct {

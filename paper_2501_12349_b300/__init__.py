@@ -297,6 +297,142 @@ class Batch:
             pass
 
 
+FP_ECANCELED = -8
+FP_REQ_REMAP, FP_REQ_PARTICLE = 0, 1
+
+
+class FpServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tick_timeout_s", ctypes.c_double)]
+
+
+class FpServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("ticks", ctypes.c_int64), ("timeouts", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("queued", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t)]
+
+
+def _server_sig():
+    L = lib()
+    if getattr(L, "_server_sig", False):
+        return L
+    P = ctypes.POINTER
+    sig = {
+        "fp_server_opts_default": ([P(FpServerOpts)], None),
+        "fp_server_create": ([P(_vp), _int, P(_vp), P(_int), P(_vp), P(FpServerOpts), P(_vp)], _int),
+        "fp_server_submit": ([_vp, _int, _int, _vp, _i64, _int, ctypes.c_double, _vp, _vp, _vp, _vp, _vp,
+                              P(_i64)], _int),
+        "fp_server_poll": ([_vp, _i64, P(_int), P(_int)], _int),
+        "fp_server_wait": ([_vp, _i64, ctypes.c_double], _int),
+        "fp_server_cancel": ([_vp, _i64], _int),
+        "fp_server_timing": ([_vp, _i64, P(ctypes.c_double), P(ctypes.c_double)], _int),
+        "fp_server_release": ([_vp, _i64], _int),
+        "fp_server_get_stats": ([_vp, P(FpServerStats)], _int),
+        "fp_server_destroy": ([_vp], _int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    L._server_sig = True
+    return L
+
+
+def fp_server_opts_default() -> FpServerOpts:
+    o = FpServerOpts()
+    _server_sig().fp_server_opts_default(ctypes.byref(o))
+    return o
+
+
+def _hptr(a):
+    """Host pointer of a numpy array or a CPU torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return _vp(a.data_ptr())
+    return _vp(a.ctypes.data)
+
+
+class Server:
+    """Continuous-batching server over resident meshes (see fp_server_*).
+    entries: list of (Mesh, remap_field or None, velocity_field or None)
+    with fields as device tensors [nc][NE][N^dr]."""
+
+    def __init__(self, entries, mem_budget: int = 1 << 30, max_active: int = 64, precision: int = FP_MIXED,
+                 tick_timeout_s: float = 30.0):
+        L = _server_sig()
+        o = fp_server_opts_default()
+        o.mem_budget, o.max_active, o.precision, o.tick_timeout_s = mem_budget, max_active, precision, tick_timeout_s
+        n = len(entries)
+        self.meshes = [e[0] for e in entries]
+        self._keep = entries
+        mh = (_vp * n)(*[e[0].handle for e in entries])
+        rf = (_vp * n)(*[None if e[1] is None else e[1].data_ptr() for e in entries])
+        nc = (_int * n)(*[0 if e[1] is None else e[1].numel() // (e[0].NE * e[0].N ** e[0].dr) for e in entries])
+        vf = (_vp * n)(*[None if e[2] is None else e[2].data_ptr() for e in entries])
+        self.handle = _vp()
+        _check("fp_server_create", L.fp_server_create(mh, n, rf, nc, vf, ctypes.byref(o), ctypes.byref(self.handle)))
+        self._bufs = {}
+
+    def submit(self, mesh: int, kind: int, pts, rk_steps: int = 0, dt: float = 0.0, outputs=None) -> int:
+        """pts: host float64 [n][d] (pinned torch tensor or numpy array);
+        outputs: (code, elem, r, dist2, out) host arrays, allocated if None."""
+        import numpy as np
+        m = self.meshes[mesh]
+        n = pts.shape[0]
+        if outputs is None:
+            ncomp = m.d if kind == FP_REQ_PARTICLE else max(1, self._nc(mesh))
+            outputs = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty((n, m.dr)), np.empty(n),
+                       np.empty((n, m.d)) if kind == FP_REQ_PARTICLE else np.empty((ncomp, n)))
+        rid = _i64(0)
+        _check("fp_server_submit", _server_sig().fp_server_submit(
+            self.handle, mesh, kind, _hptr(pts), n, rk_steps, dt, *[_hptr(a) for a in outputs], ctypes.byref(rid)))
+        self._bufs[rid.value] = (pts, outputs)
+        return rid.value
+
+    def _nc(self, mesh):
+        e = self._keep[mesh]
+        return 0 if e[1] is None else e[1].numel() // (e[0].NE * e[0].N ** e[0].dr)
+
+    def wait(self, rid: int, timeout_s: float = 60.0):
+        """Returns the request's outputs; raises FindptsError on failure or timeout."""
+        _check("fp_server_wait", _server_sig().fp_server_wait(self.handle, rid, timeout_s))
+        return self._bufs[rid][1]
+
+    def poll(self, rid: int):
+        done, st = _int(0), _int(0)
+        _check("fp_server_poll", _server_sig().fp_server_poll(self.handle, rid, ctypes.byref(done), ctypes.byref(st)))
+        return bool(done.value), st.value
+
+    def cancel(self, rid: int) -> int:
+        return _server_sig().fp_server_cancel(self.handle, rid)
+
+    def timing(self, rid: int):
+        q, t = ctypes.c_double(0), ctypes.c_double(0)
+        _check("fp_server_timing", _server_sig().fp_server_timing(self.handle, rid, ctypes.byref(q), ctypes.byref(t)))
+        return q.value, t.value
+
+    def release(self, rid: int) -> None:
+        _check("fp_server_release", _server_sig().fp_server_release(self.handle, rid))
+        self._bufs.pop(rid, None)
+
+    def stats(self) -> FpServerStats:
+        st = FpServerStats()
+        _check("fp_server_get_stats", _server_sig().fp_server_get_stats(self.handle, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self.handle is not None:
+            _check("fp_server_destroy", _server_sig().fp_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 FP_NOALLOC_MAX_POINTS = 1 << 20
 
 

@@ -899,6 +899,7 @@ extern "C" const char* fp_status_string(int s) {
     case FP_ETIMEDOUT: return "timed out";
     case FP_EBUSY: return "busy";
     case FP_EUNSUPPORTED: return "element type or order not supported";
+    case FP_ECANCELED: return "request cancelled";
     default: return "unknown status";
   }
 }

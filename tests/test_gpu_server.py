@@ -1,0 +1,169 @@
+"""The continuous-batching server: remap and particle requests over resident
+meshes, results identical alone and in a mix of concurrent requests,
+admission by device memory, host-side timeouts and cancellation."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2501_12349_b300 import workloads as W
+from parity_util import compare_eval, compare_find, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+@pytest.fixture(scope="module")
+def fp():
+    import paper_2501_12349_b300 as f
+    f.lib()
+    return f
+
+
+@pytest.fixture(scope="module")
+def resident(fp, torch):
+    rng = np.random.default_rng(50)
+    out = []
+    for n, p, A in ((6, 3, 0.2), (5, 4, 0.3), (4, 5, 0.1)):
+        coords = W.hex_mesh(n, p, A)
+        fld, _ = W.polynomial_field(coords, rng, 3)
+        vel = W.velocity_field(coords)
+        m = fp.Mesh(torch.from_numpy(coords).cuda(), 3, 3, p)
+        out.append((m, torch.from_numpy(fld).cuda(), torch.from_numpy(vel).cuda(), 1.0 / n))
+    yield out
+    for e in out:
+        e[0].close()
+
+
+def server_of(fp, resident, **kw):
+    return fp.Server([(m, f, v) for m, f, v, h in resident], **kw)
+
+
+def reference_particles(fp, torch, mesh, vel, x0, steps, dt):
+    """Explicit midpoint steps with the single-mesh GPU find + eval calls."""
+    x = torch.from_numpy(x0.copy()).cuda()
+    for _ in range(steps):
+        c, e, r, d2 = mesh.find(x)
+        u = mesh.eval(c, e, r, vel)
+        xm = x + 0.5 * dt * u.T
+        c, e, r, d2 = mesh.find(xm.contiguous())
+        u = mesh.eval(c, e, r, vel)
+        x = x + dt * u.T
+    return to_np(x), tuple(to_np(t) for t in mesh.find(x.contiguous()))
+
+
+def test_remap_matches_find_eval(fp, torch, resident):
+    s = server_of(fp, resident)
+    rng = np.random.default_rng(51)
+    pts = rng.uniform(-0.02, 1.02, (5000, 3))
+    rid = s.submit(0, fp.FP_REQ_REMAP, pts)
+    code, elem, r, d2, u = s.wait(rid)
+    m, fld, vel, h = resident[0]
+    m.set_precision(fp.FP_MIXED)
+    ref = m.find(torch.from_numpy(pts).cuda())
+    uref = to_np(m.eval(*ref[:3], fld))
+    m.set_precision(fp.FP_F64)
+    ref = tuple(to_np(t) for t in ref)
+    compare_find(ref, (code, elem, r, d2), label="server remap")
+    assert np.array_equal(ref[0], code) and np.array_equal(ref[1], elem)
+    compare_eval(to_np(fld), m.NE, m.N ** 3, elem, uref, u, "server remap eval")
+    s.close()
+
+
+def test_particles_match_reference(fp, torch, resident):
+    s = server_of(fp, resident, precision=fp.FP_F64)
+    rng = np.random.default_rng(52)
+    x0 = rng.uniform(0.02, 0.98, (2000, 3))
+    m, fld, vel, h = resident[1]
+    dt = 0.1 * h / np.sqrt(2.01)
+    rid = s.submit(1, fp.FP_REQ_PARTICLE, x0, rk_steps=4, dt=dt)
+    code, elem, r, d2, x = s.wait(rid)
+    xr, (rc, re, rr, rd) = reference_particles(fp, torch, m, vel, x0, 4, dt)
+    assert np.max(np.abs(x - xr)) < 1e-10
+    assert np.array_equal(code, rc) and np.array_equal(elem, re)
+    assert np.max(np.abs(r - rr)) < 1e-10
+    assert np.max(np.abs(x - x0)) > 0.1 * dt  # the particles moved
+    s.close()
+
+
+def test_same_alone_and_in_mix(fp, torch, resident):
+    """A request's results do not depend on what else is in flight."""
+    rng = np.random.default_rng(53)
+    pa = rng.uniform(-0.02, 1.02, (3000, 3))
+    pp = rng.uniform(0.05, 0.95, (2000, 3))
+    dt = 0.02
+    s = server_of(fp, resident)
+    alone_a = [a.copy() for a in s.wait(s.submit(2, fp.FP_REQ_REMAP, pa))]
+    alone_p = [a.copy() for a in s.wait(s.submit(0, fp.FP_REQ_PARTICLE, pp, rk_steps=3, dt=dt))]
+    ids = []
+    for k in range(40):
+        mesh = int(rng.integers(0, 3))
+        n = int(np.exp(rng.uniform(np.log(100), np.log(20000))))
+        if k % 2:
+            ids.append(s.submit(mesh, fp.FP_REQ_REMAP, rng.uniform(-0.02, 1.02, (n, 3))))
+        else:
+            ids.append(s.submit(mesh, fp.FP_REQ_PARTICLE, rng.uniform(0.05, 0.95, (n, 3)), rk_steps=2, dt=dt))
+        if k == 10:
+            ra = s.submit(2, fp.FP_REQ_REMAP, pa)
+        if k == 20:
+            rp = s.submit(0, fp.FP_REQ_PARTICLE, pp, rk_steps=3, dt=dt)
+    mix_a = s.wait(ra)
+    mix_p = s.wait(rp)
+    for i in ids:
+        s.wait(i)
+    st = s.stats()
+    assert st.completed == 44 and st.active == 0 and st.bytes_in_use == 0
+    assert st.ticks < 44 * 5  # stages of different requests shared ticks
+    for a, b in zip(alone_a, mix_a):
+        assert np.array_equal(a, b)
+    for a, b in zip(alone_p, mix_p):
+        assert np.array_equal(a, b)
+    s.close()
+
+
+def test_admission_by_memory(fp, torch, resident):
+    budget = 4 << 20
+    s = server_of(fp, resident, mem_budget=budget)
+    rng = np.random.default_rng(54)
+    with pytest.raises(fp.FindptsError) as err:
+        s.submit(0, fp.FP_REQ_REMAP, rng.uniform(0, 1, (200000, 3)))  # can never fit
+    assert err.value.status == fp.FP_ENOMEM
+    peak = [0]
+    stop = threading.Event()
+
+    def watch():
+        while not stop.is_set():
+            peak[0] = max(peak[0], s.stats().bytes_in_use)
+
+    th = threading.Thread(target=watch)
+    th.start()
+    ids = [s.submit(i % 3, fp.FP_REQ_REMAP, rng.uniform(0, 1, (20000, 3))) for i in range(12)]
+    for i in ids:
+        s.wait(i)
+    stop.set()
+    th.join()
+    assert 0 < peak[0] <= budget
+    assert s.stats().completed == 12
+    s.close()
+
+
+def test_wait_timeout_and_cancel(fp, torch, resident):
+    s = server_of(fp, resident, max_active=1)
+    rng = np.random.default_rng(55)
+    big = s.submit(0, fp.FP_REQ_PARTICLE, rng.uniform(0.05, 0.95, (200000, 3)), rk_steps=20, dt=0.001)
+    small = s.submit(1, fp.FP_REQ_REMAP, rng.uniform(0, 1, (100, 3)))
+    with pytest.raises(fp.FindptsError) as err:
+        s.wait(small, timeout_s=1e-4)
+    assert err.value.status == fp.FP_ETIMEDOUT
+    rc = s.cancel(small)
+    if rc == 0:
+        assert s.poll(small) == (True, fp.FP_ECANCELED)
+    s.wait(big, timeout_s=120)
+    assert s.stats().timeouts == 0
+    s.close()
