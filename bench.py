@@ -281,6 +281,155 @@ def batch_block(fp, W, torch, dev, st, flush, args):
     return res
 
 
+def serve_block(fp, W, torch, dev, args):
+    """Serving: 8 resident hex meshes (p = 3..7, 1e4-1e5 elements); requests
+    of log-uniform size 1e2-1e6, half remap (find + interpolate a scalar
+    field), half particle (4 explicit-midpoint steps through the interpolated
+    velocity u = (sin pi x cos pi y, -cos pi x sin pi y, 0.1), dt = 0.1 h_min /
+    |u|_max).  First a burst measures the served capacity, then Poisson
+    arrivals at 0.5, 0.7 and 0.9 of it give latency percentiles.  Results of
+    the load requests land in a shared pinned host sink (timing only)."""
+    t0 = time.perf_counter()
+    ws = W.config5_meshes()
+    entries, meshes = [], []
+    for w in ws:
+        m = fp.Mesh(torch.from_numpy(w.coords).to(dev), 3, 3, w.order)
+        meshes.append(m)
+        entries.append((m, torch.from_numpy(w.field).to(dev), torch.from_numpy(W.velocity_field(w.coords)).to(dev)))
+    gen_s = time.perf_counter() - t0
+    h_min = min(w.h for w in ws)
+    dt = 0.1 * h_min / np.sqrt(1.01)
+    srv = fp.Server(entries, mem_budget=8 << 30, max_active=64, precision=fp.FP_MIXED)
+    rng = np.random.default_rng(5)
+    nmax = 10 ** 6
+    pool_r = torch.from_numpy(rng.uniform(-0.01, 1.01, (nmax, 3))).pin_memory()
+    pool_p = torch.from_numpy(rng.uniform(0.05, 0.95, (nmax, 3))).pin_memory()
+    sink = (torch.empty(nmax, dtype=torch.int32).pin_memory(), torch.empty(nmax, dtype=torch.int32).pin_memory(),
+            torch.empty((nmax, 3), dtype=torch.float64).pin_memory(), torch.empty(nmax, dtype=torch.float64).pin_memory(),
+            torch.empty((nmax, 3), dtype=torch.float64).pin_memory())
+
+    def draw(k):
+        out = []
+        for _ in range(k):
+            n = int(np.exp(rng.uniform(np.log(1e2), np.log(1e6))))
+            kind = fp.FP_REQ_REMAP if rng.integers(0, 2) == 0 else fp.FP_REQ_PARTICLE
+            mesh = int(rng.integers(0, len(ws)))
+            off = int(rng.integers(0, nmax - n + 1))
+            out.append((mesh, kind, n, off))
+        return out
+
+    def submit(req):
+        mesh, kind, n, off = req
+        pool = pool_r if kind == fp.FP_REQ_REMAP else pool_p
+        return srv.submit(mesh, kind, pool[off:off + n], rk_steps=4 if kind else 0, dt=dt, outputs=sink)
+
+    def stage_points(reqs):
+        return sum(n * (1 if k == fp.FP_REQ_REMAP else 9) for _, k, n, _ in reqs)
+
+    def collect(ids):
+        lat = []
+        for i in ids:
+            srv.wait(i, timeout_s=600)
+            lat.append(srv.timing(i)[1])
+            srv.release(i)
+        return lat
+
+    res = {"workload": "8 hex meshes p=3..7 NE 1e4-1e5; requests 1e2-1e6 pts, half remap, half particle (4 RK2 steps)",
+           "generate_and_setup_s": gen_s, "precision": "mixed", "dt": dt}
+    burst = draw(args.serve_burst)
+
+    def serial_f64(reqs):
+        """The same requests one at a time through the plain FP64 calls:
+        upload, find + eval per stage (particles: midpoint steps with a torch
+        update), download."""
+        st = torch.cuda.current_stream()
+        for mesh, kind, n, off in reqs:
+            m, fld, vel = entries[mesh]
+            pool = pool_r if kind == fp.FP_REQ_REMAP else pool_p
+            x = pool[off:off + n].to(dev, non_blocking=True)
+            code = torch.empty(n, dtype=torch.int32, device=dev)
+            elem = torch.empty(n, dtype=torch.int32, device=dev)
+            r = torch.empty((n, 3), dtype=torch.float64, device=dev)
+            d2 = torch.empty(n, dtype=torch.float64, device=dev)
+            if kind == fp.FP_REQ_REMAP:
+                u = torch.empty((1, n), dtype=torch.float64, device=dev)
+                fp.fp_findpts(m.handle, x, code, elem, r, d2)
+                fp.fp_eval(m.handle, code, elem, r, fld, 1, u)
+                sink[4].view(-1)[:n].copy_(u.view(-1), non_blocking=True)
+            else:
+                u = torch.empty((3, n), dtype=torch.float64, device=dev)
+                for _ in range(4):
+                    fp.fp_findpts(m.handle, x, code, elem, r, d2)
+                    fp.fp_eval(m.handle, code, elem, r, vel, 3, u)
+                    xm = (x + 0.5 * dt * u.T).contiguous()
+                    fp.fp_findpts(m.handle, xm, code, elem, r, d2)
+                    fp.fp_eval(m.handle, code, elem, r, vel, 3, u)
+                    x = (x + dt * u.T).contiguous()
+                fp.fp_findpts(m.handle, x, code, elem, r, d2)
+                sink[4][:n].copy_(x, non_blocking=True)
+            sink[0][:n].copy_(code, non_blocking=True)
+            sink[1][:n].copy_(elem, non_blocking=True)
+            sink[2][:n].copy_(r, non_blocking=True)
+            sink[3][:n].copy_(d2, non_blocking=True)
+        st.synchronize()
+
+    t0 = time.perf_counter()
+    serial_f64(burst)
+    wall_serial = time.perf_counter() - t0
+    res["serial_f64_same_requests"] = {"wall_s": wall_serial, "requests_per_s": len(burst) / wall_serial,
+                                       "stage_points_per_s": stage_points(burst) / wall_serial}
+
+    def burst_run(server):
+        t0 = time.perf_counter()
+        ids = []
+        for q in burst:
+            mesh, kind, n, off = q
+            pool = pool_r if kind == fp.FP_REQ_REMAP else pool_p
+            ids.append(server.submit(mesh, kind, pool[off:off + n], rk_steps=4 if kind else 0, dt=dt, outputs=sink))
+        for i in ids:
+            server.wait(i, timeout_s=600)
+            server.release(i)
+        return time.perf_counter() - t0
+
+    srv64 = fp.Server(entries, mem_budget=8 << 30, max_active=64, precision=fp.FP_F64)
+    wall64 = burst_run(srv64)
+    srv64.close()
+    res["served_f64_capacity"] = {"wall_s": wall64, "requests_per_s": len(burst) / wall64,
+                                  "stage_points_per_s": stage_points(burst) / wall64}
+    wall = burst_run(srv)
+    cap_rps = len(burst) / wall
+    res["capacity"] = {"requests": len(burst), "wall_s": wall, "requests_per_s": cap_rps,
+                       "request_points_per_s": sum(q[2] for q in burst) / wall,
+                       "stage_points_per_s": stage_points(burst) / wall,
+                       "speedup_vs_serial_f64": wall_serial / wall,
+                       "speedup_vs_served_f64": wall64 / wall}
+    res["load"] = []
+    for rho in (0.5, 0.7, 0.9):
+        reqs = draw(args.serve_requests)
+        lam = rho * cap_rps
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
+        ids = []
+        t0 = time.perf_counter()
+        for a, q in zip(arrivals, reqs):
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            ids.append(submit(q))
+        lat = collect(ids)
+        wall = time.perf_counter() - t0
+        res["load"].append({"rho": rho, "arrival_rate_rps": lam, "requests": len(reqs), "wall_s": wall,
+                            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                            "mean_ms": 1e3 * float(np.mean(lat)),
+                            "request_points_per_s": sum(q[2] for q in reqs) / wall,
+                            "stage_points_per_s": stage_points(reqs) / wall})
+    st = srv.stats()
+    res["server"] = {"ticks": st.ticks, "completed": st.completed, "timeouts": st.timeouts}
+    srv.close()
+    for m in meshes:
+        m.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,6 +440,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-mixed", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-burst", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -414,6 +566,7 @@ def main():
     mesh.close()
     mixed = None if args.skip_mixed else mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist)
     batched = None if (args.skip_batch or rank != 0) else batch_block(fp, W, torch, dev, st, flush, args)
+    serving = None if (args.skip_serve or rank != 0) else serve_block(fp, W, torch, dev, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -438,7 +591,7 @@ def main():
                               "beta_iterations": int(sv[3]), "per_point_iterations": float(sv[1]) / n},
             "setup_ms": setup_ms, "wall_s_timed": wall, "device_status": status,
             "e2e": {"value": e2e_v, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "cpu_baseline": cpu, "clocks": clk, "mixed": mixed, "batched": batched,
+            "cpu_baseline": cpu, "clocks": clk, "mixed": mixed, "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -75,7 +75,7 @@ int launch_eval_class(const BatchItem* items, int nitems, int64_t total, int N, 
 }
 
 struct Tuning {
-  int ctas_per_sm = 2;
+  int ctas_per_sm = 2;  // default; fp_batch_autotune may pick 1-3
   int clog2 = 5;
   float ms = -1.f;  // measured time of the chosen shape, -1 if untuned
 };
@@ -293,7 +293,8 @@ extern "C" int fp_batch_autotune(fp_batch b, void* stream) {
   using namespace fp;
   if (!b) return FP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const int ctas[2] = {1, 2};
+  // CTAs per SM: the FP64 kernel holds 2 per SM, the mixed one 3
+  const int ctas[2] = {b->precision == FP_MIXED ? 2 : 1, b->precision == FP_MIXED ? 3 : 2};
   const int clogs[3] = {5, 7, 9};
   cudaEvent_t e0, e1;
   FP_CUDA_TRY(cudaEventCreate(&e0));

@@ -117,7 +117,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
       } else {
         const bool beta = (l > 0) && at_bound<DR>(r);
         double HS[DR][DR];
-        if (beta) {
+        if (beta && !hess_term_slice<N, D, DR, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r, dx, G, HS)) {
           hess_term<N, D, DR, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r, dx, ts, HS);
         }
         double ds[DR];

@@ -115,25 +115,18 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
         ++cnt.v[0];
         rel_point<D>(*mp, e, xs, xr);
         xrel = __ldg(mp->box32 + (int64_t)e * BOX32 + 18);
-        // closest node in FP32 (the start only changes the path, not the
-        // converged result, and FP64 decides everything that matters)
-        const float* X32 = mp->coords32 + (int64_t)e * NN;
-        float b1 = INFINITY;
-        int nb = 0;
-#pragma unroll 4
-        for (int nn = 0; nn < NN; ++nn) {
-          float d = 0.f;
+        // start from the linearised map, r0 = clamp(T (x* - x(0))): the FP32
+        // phase promises the converged result, not the FP64 path's iterates
+        {
+          const float* rec = mp->box32 + (int64_t)e * BOX32;
 #pragma unroll
-          for (int c = 0; c < D; ++c) {
-            const float t = xr[c] - __ldg(X32 + c * mp->cstride + nn);
-            d = fmaf(t, t, d);
-          }
-          if (d < b1) {
-            b1 = d;
-            nb = nn;
+          for (int j = 0; j < DR; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) v = fmaf(__ldg(rec + 23 + j * 3 + c), xr[c] - __ldg(rec + 20 + c), v);
+            r[j] = fminf(1.f, fmaxf(-1.f, v));
           }
         }
-        node_coords<N, DR, float>(B, nb, r);
         etype = X_INIT;
         need = true;
         break;
@@ -150,7 +143,8 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
       } else {
         const bool beta = (l > 0) && at_bound<DR>(r);
         float HS[DR][DR];
-        if (beta) hess_term<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, ts32, HS);
+        if (beta && !hess_term_slice<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, G, HS))
+          hess_term<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, ts32, HS);
         float ds[DR];
         bool used_beta;
         const float mx = newton_step<D, DR, float>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
@@ -306,8 +300,10 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
   cnt.flush(stats);
 }
 
+constexpr int kMixedCtasPerSm = 3;
+
 template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, 2)
+__global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
     k_find_mixed(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
                  int64_t n, int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
                  double* __restrict__ dist2, int* __restrict__ queue, int* __restrict__ qcount,
@@ -317,7 +313,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
 }
 
 template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, 2)
+__global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
     k_find_mixed_batch(const BatchItem* __restrict__ items, int nitems, int64_t total, const BasisTab B,
                        int* __restrict__ queue, int* __restrict__ qcount, int clog2,
                        unsigned long long* stats) {
@@ -338,11 +334,10 @@ int find_mixed(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int*
   if (rc == FP_OK)
     rc = dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
       constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
-      const int blocks = persistent_blocks(n, 2);
-      k_find_mixed<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, n, code, elem, r,
-                                                              dist2, queue, qcount, stats);
-      k_find_f64<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount, code,
-                                                            elem, r, dist2, stats);
+      k_find_mixed<N, D, DR><<<persistent_blocks(n, kMixedCtasPerSm), kFindThreads, 0, st>>>(
+          v, m->basis, pts, n, code, elem, r, dist2, queue, qcount, stats);
+      k_find_f64<N, D, DR><<<persistent_blocks(n, 2), kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount,
+                                                                             code, elem, r, dist2, stats);
       return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
     });
   cudaFreeAsync(queue, st);
@@ -361,11 +356,10 @@ int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, int64_t n, in
   const DevMesh v = m->view();
   return dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
-    const int blocks = persistent_blocks(n, 2);
-    k_find_mixed<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, n, code, elem, r, dist2,
-                                                            queue, qcount, stats);
-    k_find_f64<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount, code,
-                                                          elem, r, dist2, stats);
+    k_find_mixed<N, D, DR><<<persistent_blocks(n, kMixedCtasPerSm), kFindThreads, 0, st>>>(
+        v, m->basis, pts, n, code, elem, r, dist2, queue, qcount, stats);
+    k_find_f64<N, D, DR><<<persistent_blocks(n, 2), kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount,
+                                                                           code, elem, r, dist2, stats);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
   });
 }
@@ -385,8 +379,8 @@ int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N,
     if (precision == FP_MIXED) {
       k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, B, queue, qcount,
                                                                      clog2, stats);
-      k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, queue, qcount, B,
-                                                                   clog2, stats);
+      k_find_f64_batch<NN, D, DR><<<persistent_blocks(total, 2), kFindThreads, 0, st>>>(
+          items, nitems, total, queue, qcount, B, clog2, stats);
     } else {
       k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, nullptr, nullptr, B,
                                                                    clog2, stats);

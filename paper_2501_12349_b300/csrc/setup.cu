@@ -230,7 +230,7 @@ template <int N, int D, int DR>
 __global__ void __launch_bounds__(kBoxThreads)
     k_boxes(const double* __restrict__ coords, int64_t NE, const double* __restrict__ tab, int M,
             BasisTab B, double tol, double* __restrict__ aabb, double* __restrict__ obb_c,
-            double* __restrict__ obb_A, int* status) {
+            double* __restrict__ obb_A, double* __restrict__ linmap, int* status) {
   constexpr int NN = (DR == 3) ? N * N * N : N * N;
   constexpr int NPIECE = (DR == 3) ? 6 : (D == 2 ? 4 : 1);
   constexpr int PIECE = (DR == 3 || D == 3) ? N * N : N;  // values per piece
@@ -435,6 +435,10 @@ __global__ void __launch_bounds__(kBoxThreads)
       aabb[e * 2 * D + c] = mid[c] - hw[c];
       aabb[e * 2 * D + D + c] = mid[c] + hw[c];
     }
+    for (int c = 0; c < D; ++c) {
+      linmap[e * 12 + c] = xc[c];
+      for (int q = 0; q < D; ++q) linmap[e * 12 + 3 + c * 3 + q] = T[c * D + q];
+    }
     expand(D, blo[1], bhi[1], tol, mid, hw);
     for (int c = 0; c < D; ++c) {
       double s = xc[c];
@@ -569,11 +573,12 @@ __global__ void k_coords32(const double* __restrict__ x, const double* __restric
 }
 
 // FP32 record per element (layout fp::BOX32): lo[3] hi[3] c[3] A[3][3] Xrel
-// pad, rounded to nearest (the certified FP32 tests carry their own
-// margins); Xrel = largest AABB half-width, slightly enlarged, bounds
-// |x - x_ref| over the element.
+// pad xc[3] T[3][3], rounded to nearest (the certified FP32 tests carry
+// their own margins); Xrel = largest AABB half-width, slightly enlarged,
+// bounds |x - x_ref| over the element; xc = x(0) - x_ref; T the OBB frame.
 __global__ void k_box32(const double* __restrict__ aabb, const double* __restrict__ obb_c,
-                        const double* __restrict__ obb_A, int64_t NE, int d, float* __restrict__ out) {
+                        const double* __restrict__ obb_A, const double* __restrict__ lin, int64_t NE,
+                        int d, float* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < NE;
        e += (int64_t)gridDim.x * blockDim.x) {
     float* o = out + e * BOX32;
@@ -587,6 +592,10 @@ __global__ void k_box32(const double* __restrict__ aabb, const double* __restric
       for (int k = 0; k < d; ++k) o[9 + c * 3 + k] = (float)obb_A[(e * d + c) * d + k];
     }
     o[18] = (float)(X * (1.0 + 1e-6));
+    for (int c = 0; c < d; ++c) {
+      o[20 + c] = (float)(lin[e * 12 + c] - elem_ref(aabb, d, e, c));
+      for (int q = 0; q < d; ++q) o[23 + c * 3 + q] = (float)lin[e * 12 + 3 + c * 3 + q];
+    }
   }
 }
 
@@ -652,7 +661,12 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
   // element boxes
   const std::vector<double> htab = bound_tables(m->N, m->M);
   double* dtab = nullptr;
+  double* dlin = nullptr;  // per element x(0) and the OBB frame T, for box32
   FP_CUDA_TRY(cudaMalloc(&dtab, htab.size() * sizeof(double)));
+  if (cudaMalloc(&dlin, sizeof(double) * 12 * m->NE) != cudaSuccess) {
+    cudaFree(dtab);
+    return FP_ENOMEM;
+  }
   int rc = FP_OK;
   do {
     if (cudaMemcpyAsync(dtab, htab.data(), htab.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
@@ -664,7 +678,7 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
       constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
       k_boxes<N, D, DR><<<(unsigned)m->NE, kBoxThreads, 0, st>>>(
           m->coords, m->NE, dtab, m->M, m->basis, m->opts.bbox_tol, m->aabb, m->obb_c, m->obb_A,
-          m->status);
+          dlin, m->status);
       return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
     });
     if (rc != FP_OK) break;
@@ -742,13 +756,15 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
       cudaFree(counts);
       break;
     }
-    k_box32<<<grid_for(m->NE, 256, 148 * 16), 256, 0, st>>>(m->aabb, m->obb_c, m->obb_A, m->NE, m->d,
-                                                            m->box32);
+    k_box32<<<grid_for(m->NE, 256, 148 * 16), 256, 0, st>>>(m->aabb, m->obb_c, m->obb_A, dlin, m->NE,
+                                                            m->d, m->box32);
     ce = cudaStreamSynchronize(st);
     cudaFree(counts);
     if (ce != cudaSuccess) rc = FP_ELAUNCH;
   } while (0);
+  cudaStreamSynchronize(st);
   cudaFree(dtab);
+  cudaFree(dlin);
   return rc;
 }
 
