@@ -36,25 +36,62 @@ METRIC = "located+evaluated points/s (3D hex p=4)"
 WORKLOAD = "hex3d_32^3_p4_kershaw0.3_1e6pts"
 
 
-def flop_model(stats, N, d, dr, n_found, nc):
-    """Algorithmic FP64 flops (FMA = 2) of one find launch and one eval launch,
-    from the find counters: candidates C, iterations I, beta iterations B."""
+# DRAM bytes (read + write) of one k_find_f64 launch on the 32^3 p=4 mesh with
+# 10^6 points, from one ncu capture of the current kernel (the summary under
+# profiles/ gives the command); None once the kernel changes.
+F64_TRAFFIC = 302.499328e6 + 77.894656e6
+
+
+def flop_terms(N, d, dr):
+    """Flops (FMA = 2) of the per-point building blocks: x and G by sum
+    factorisation (eval_g), the beta term restricted to the face (edge in
+    2D) the iterate is held on (hess), one interpolated component
+    (eval_x), the box tests, the closest-node search, the Newton step
+    algebra."""
     ne = N ** dr
     if dr == 3:
         eval_g = d * 2 * (N * N * (2 * N + 3) + 4 * N) + dr * 8 * N
-        hess = d * 2 * (N * N * (3 * N + 6) + 6 * N) + dr * 12 * N
+        hess = d * 2 * (3 * N * N + 3 * N) + 2 * 12 * N + 6 * d
         eval_x = 2 * (N ** 3 + N ** 2 + N) + dr * 4 * N
     else:
         eval_g = d * 2 * (N * (2 * N + 3)) + dr * 8 * N
-        hess = d * 2 * (N * (3 * N + 6)) + dr * 12 * N
+        hess = d * 2 * N + 12 * N + 2 * d
         eval_x = 2 * (N ** 2 + N) + dr * 4 * N
-    C, I, B = int(stats[0]), int(stats[1]), int(stats[3])
-    box = 2 * d * d + d
-    node = 3 * d * ne
-    newton_alg = 60
-    find = C * (box + node + eval_g) + I * (eval_g + newton_alg) + B * hess
-    ev = n_found * (nc * (eval_x - dr * 4 * N) + dr * 4 * N)
-    return float(find), float(ev)
+    return {"eval_g": eval_g, "hess": hess, "eval_x": eval_x, "box": 2 * d * d + d,
+            "node": 3 * d * ne, "newton": 60, "basis": dr * 4 * N}
+
+
+def find_flops(stats, N, d, dr, node=True):
+    """Algorithmic flops of a find from its counters: candidates C, Newton
+    steps I, steps with the beta term B, evaluations of x and G (one per
+    candidate and one per trial step; re-evaluations after rejected steps
+    are not counted)."""
+    t = flop_terms(N, d, dr)
+    C, I, B, EV = int(stats[0]), int(stats[1]), int(stats[3]), int(stats[7])
+    return C * (t["box"] + (t["node"] if node else 0)) + EV * t["eval_g"] + I * t["newton"] + B * t["hess"]
+
+
+def flop_model(stats, N, d, dr, n_found, nc):
+    """Algorithmic FP64 flops of one find launch and one eval launch."""
+    t = flop_terms(N, d, dr)
+    ev = n_found * (nc * (t["eval_x"] - t["basis"]) + t["basis"])
+    # the closest-node search runs on the FP32 pipe (certified, FP64 only
+    # inside its rounding margin), so it is not counted as FP64 work
+    return float(find_flops(stats, N, d, dr, node=False)), float(ev)
+
+
+def mixed_flop_model(stats, N, d, dr):
+    """(FP32, FP64) algorithmic flops of one mixed-precision find: the FP32
+    kernel's candidates, steps and evaluations (linearised initial guess
+    instead of the node search), its FP64 refinements (x(r) in d
+    components, residual, normal equations, solve), and the FP64 kernel on
+    the handed-over points (counters [8]-[15])."""
+    t = flop_terms(N, d, dr)
+    C, R = int(stats[0]), int(stats[4])
+    f32 = C * 2 * d * dr + find_flops(stats[0:8], N, d, dr, node=False)
+    refine = d * (t["eval_x"] - t["basis"]) + t["basis"] + 2 * d + 2 * d * dr * (dr + 1) + 30
+    f64 = R * refine + find_flops(stats[8:16], N, d, dr, node=False)
+    return float(f32), float(f64)
 
 
 class ClockSampler:
@@ -157,7 +194,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist):
+def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, peaks):
     """The 10^7-point, 3-component workload on the same mesh, find + eval,
     timed with the FP64 path and with the mixed path (FP32 filter and early
     Newton, FP64 final steps); both results are checked against each other."""
@@ -202,17 +239,27 @@ def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist):
         fp.fp_findpts_stats(mesh.handle, pts, code, elem, r, d2, stats)
         sv = stats.cpu().numpy()
         outs[prec] = (code.clone(), elem.clone(), r.clone())
+        fsec = statistics.mean(fms) / 1e3
+        if prec == "f64":
+            f32, f64 = 0.0, find_flops(sv, w.N, 3, 3, node=False)
+        else:
+            f32, f64 = mixed_flop_model(sv, w.N, 3, 3)
         res[prec] = {"value": world * n * steps / t, "unit": "points/s",
                      "find_ms": statistics.mean(fms), "eval_ms": statistics.mean(ems),
+                     "pipes": {"fp64": {"achieved": f64 / fsec / 1e12, "frac": f64 / fsec / 1e12 / peaks[0]},
+                               "fp32": {"achieved": f32 / fsec / 1e12, "frac": f32 / fsec / 1e12 / peaks[1]},
+                               "unit": "TFLOP/s", "time": "whole find call (all its kernels)"},
                      "counters": {"candidates": int(sv[0]), "iterations": int(sv[1]),
                                   "fp64_refine_evals": int(sv[4]), "fp64_box_tests": int(sv[5]),
-                                  "to_fp64_kernel": int(sv[6])}}
+                                  "to_fp64_kernel": int(sv[6]), "fp64_kernel_candidates": int(sv[8]),
+                                  "fp64_kernel_iterations": int(sv[9])}}
     a, b = outs["f64"], outs["mixed"]
     same = (a[0] == b[0]) & (a[1] == b[1])
     res["code_elem_mismatch_vs_f64"] = int((~same).sum().item())
     found = same & (a[0] != 2)
     res["max_abs_dr_vs_f64"] = float((a[2] - b[2]).abs().max(dim=1).values[found].max().item())
     res["speedup_vs_f64"] = res["mixed"]["value"] / res["f64"]["value"]
+    res["peaks_tflops"] = {"fp64": peaks[0], "fp32": peaks[1]}
     res["status"] = mesh.device_status()
     mesh.close()
     return res
@@ -529,9 +576,20 @@ def main():
     n_found = int((code != 2).sum().item())
     fl_find, fl_eval = flop_model(sv, w.N, 3, 3, n_found, 1)
     peak64 = fp.fp_alu_peak(0, 4000) / 1e3  # TFLOP/s
+    peak32 = fp.fp_alu_peak(1, 4000) / 1e3
     find_avg = statistics.mean(find_ms) / 1e3
     eval_avg = statistics.mean(eval_ms) / 1e3
-    ach = fl_find / find_avg / 1e12
+    peak_src = "FP64 FMA pipe, measured live by fp_alu_peak (no FP64 entry in the measured peaks file)"
+    if args.precision == "f64":
+        ach = fl_find / find_avg / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
+                    "traffic": F64_TRAFFIC, "kernel": "k_find_f64", "peak_source": peak_src}
+    else:
+        f32, f64 = mixed_flop_model(sv, w.N, 3, 3)
+        a64, a32 = f64 / find_avg / 1e12, f32 / find_avg / 1e12
+        roofline = {"bound": "alu", "achieved": a64, "peak": peak64, "unit": "TFLOP/s", "frac": a64 / peak64,
+                    "traffic": None, "kernel": "k_find_mixed + k_find_f64 (FP64 pipe)", "peak_source": peak_src,
+                    "fp32": {"achieved": a32, "peak": peak32, "frac": a32 / peak32}}
 
     # end to end through host buffers: pinned H2D of the points, find + eval,
     # D2H of code, elem, r, dist2 and the interpolated values
@@ -564,7 +622,7 @@ def main():
     e2e_v = world * n * args.steps / e2e_t
     status = mesh.device_status()
     mesh.close()
-    mixed = None if args.skip_mixed else mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist)
+    mixed = None if args.skip_mixed else mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, (peak64, peak32))
     batched = None if (args.skip_batch or rank != 0) else batch_block(fp, W, torch, dev, st, flush, args)
     serving = None if (args.skip_serve or rank != 0) else serve_block(fp, W, torch, dev, args)
 
@@ -581,14 +639,13 @@ def main():
                        "nc": 1, "l2": "flushed (256 MB write) before each timed step",
                        "parallelism": f"replicas{world}"},
             "gpu_launches": 2 * args.steps,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
-                         "frac": ach / peak64, "traffic": None, "kernel": "k_find_f64",
-                         "peak_source": "FP64 FMA pipe, measured live by fp_alu_peak (no FP64 entry in MEASURED_PEAKS.json)"},
+            "roofline": roofline,
             "kernels_ms": {"find": statistics.mean(find_ms), "eval": statistics.mean(eval_ms)},
             "eval_roofline": {"bound": "alu", "achieved": fl_eval / eval_avg / 1e12, "peak": peak64,
                               "unit": "TFLOP/s", "frac": fl_eval / eval_avg / 1e12 / peak64},
             "find_counters": {"candidates": int(sv[0]), "iterations": int(sv[1]), "rejected": int(sv[2]),
-                              "beta_iterations": int(sv[3]), "per_point_iterations": float(sv[1]) / n},
+                              "beta_iterations": int(sv[3]), "evaluations": int(sv[7]),
+                              "per_point_iterations": float(sv[1]) / n},
             "setup_ms": setup_ms, "wall_s_timed": wall, "device_status": status,
             "e2e": {"value": e2e_v, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "cpu_baseline": cpu, "clocks": clk, "mixed": mixed, "batched": batched, "serving": serving,

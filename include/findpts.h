@@ -70,6 +70,18 @@ extern "C" {
 
 #define FP_MAX_N 8 /* orders 1..7 */
 
+/* Traversal order of the query points inside fp_findpts.  FP_ORDER_CELL
+ * groups the points by their Psi_L cell before the find kernels run (a
+ * counting sort on the device, for calls of at least 16384 points), so the
+ * points a warp handles share candidate elements; the paper's remark on the
+ * CPU implementation (Sec. 3.2) that processing the points of an element
+ * together improves locality.  FP_ORDER_GIVEN takes the points as given.
+ * The outputs are identical either way; only the speed differs.  The cell
+ * order needs 8 bytes per point plus 8 bytes per cell of scratch, taken from
+ * the stream-ordered allocator for the duration of the call. */
+#define FP_ORDER_GIVEN 0
+#define FP_ORDER_CELL 1
+
 typedef struct fp_mesh_s* fp_mesh; /* opaque; library-owned; device-resident */
 
 /* Options of Setup and Find.  fp_opts_default fills the paper's defaults. */
@@ -81,6 +93,7 @@ typedef struct {
   int max_iter;      /* Newton iteration cap per candidate (Sec. 3.2.1: 50)        */
   double dist_tol;   /* surfaces: INTERIOR needs dist2 < dist_tol (Sec. 4.4: 1e-10) */
   int precision;     /* FP_F64 or FP_MIXED                                          */
+  int point_order;   /* FP_ORDER_CELL (default) or FP_ORDER_GIVEN, see below        */
 } fp_opts;
 
 void fp_opts_default(fp_opts* opts);
@@ -101,6 +114,10 @@ int fp_free(fp_mesh m);
  * FP_MIXED (both sets of device data are built by fp_setup).  Host call. */
 int fp_set_precision(fp_mesh m, int precision);
 
+/* Sets the point traversal order (FP_ORDER_GIVEN / FP_ORDER_CELL) of later
+ * fp_findpts calls on m.  Errors: FP_EINVAL. */
+int fp_set_point_order(fp_mesh m, int order);
+
 /* Find (Sec. 3.2) for n points pts_dev ([n][d] FP64).  Outputs (device):
  *   code[n]  FP_INTERIOR / FP_BORDER / FP_NOT_FOUND
  *   elem[n]  element id, -1 when NOT_FOUND
@@ -114,11 +131,15 @@ int fp_findpts(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
 /* As fp_findpts, and adds this call's counters into stats_dev (device,
  * FP_NSTATS uint64 values, caller-zeroed):
  *   [0] candidates that passed the box filter  [1] Newton iterations
- *   [2] rejected trust-region steps            [3] iterations with beta = 1
+ *   [2] rejected trust-region steps            [3] Newton steps with beta = 1
  *   [4] FP64 refinement evaluations (mixed)    [5] box tests decided in FP64
  *   [6] points the mixed path handed to its FP64 kernel
- * (with FP_MIXED, [1]-[3] count FP32 and FP64 iterations together). */
-#define FP_NSTATS 8
+ *   [7] evaluations of x(r) and G(r): one per candidate plus one per trial
+ *       step (re-evaluations after a rejected step are not counted)
+ * With FP_MIXED, [0]-[7] count the FP32 kernel (its iterations are FP32
+ * iterations) and [8]-[15] count, in the same layout, the FP64 kernel that
+ * finishes the points of [6]; with FP_F64, [8]-[15] stay zero. */
+#define FP_NSTATS 16
 int fp_findpts_stats(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
                      int32_t* elem, double* r, double* dist2, uint64_t* stats_dev,
                      void* stream);

@@ -19,8 +19,9 @@ FP_OK, FP_EINVAL, FP_ENOMEM, FP_ELAUNCH, FP_EDEVICE, FP_ETIMEDOUT, FP_EBUSY, FP_
     0, -1, -2, -3, -4, -5, -6, -7)
 FP_INTERIOR, FP_BORDER, FP_NOT_FOUND = 0, 1, 2
 FP_F64, FP_MIXED = 0, 1
+FP_ORDER_GIVEN, FP_ORDER_CELL = 0, 1
 FP_MAX_N = 8
-FP_NSTATS = 8
+FP_NSTATS = 16
 
 
 class FindptsError(RuntimeError):
@@ -32,7 +33,7 @@ class FindptsError(RuntimeError):
 class FpOpts(ctypes.Structure):
     _fields_ = [("bbox_tol", ctypes.c_double), ("M", ctypes.c_int), ("n_grid", ctypes.c_int),
                 ("newton_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("dist_tol", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("dist_tol", ctypes.c_double), ("precision", ctypes.c_int), ("point_order", ctypes.c_int)]
 
 
 class FpMeshInfo(ctypes.Structure):
@@ -60,6 +61,7 @@ def lib() -> ctypes.CDLL:
             "fp_setup": ([_vp, _int, _int, _int, _i64, ctypes.POINTER(FpOpts), _vp, ctypes.POINTER(_vp)], _int),
             "fp_free": ([_vp], _int),
             "fp_set_precision": ([_vp, _int], _int),
+            "fp_set_point_order": ([_vp, _int], _int),
             "fp_findpts": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _int),
             "fp_findpts_stats": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fp_eval": ([_vp, _vp, _vp, _vp, _i64, _vp, _int, _vp, _vp], _int),
@@ -133,6 +135,10 @@ def fp_set_precision(mesh, precision: int) -> None:
     _check("fp_set_precision", lib().fp_set_precision(mesh, int(precision)))
 
 
+def fp_set_point_order(mesh, order: int) -> None:
+    _check("fp_set_point_order", lib().fp_set_point_order(mesh, int(order)))
+
+
 def fp_findpts(mesh, pts, code, elem, r, dist2, stream=None) -> None:
     import torch
     n = pts.shape[0] if pts.dim() > 0 else 0
@@ -145,6 +151,8 @@ def fp_findpts(mesh, pts, code, elem, r, dist2, stream=None) -> None:
 def fp_findpts_stats(mesh, pts, code, elem, r, dist2, stats, stream=None) -> None:
     import torch
     n = pts.shape[0] if pts.dim() > 0 else 0
+    if stats.numel() < FP_NSTATS:
+        raise ValueError(f"stats: need {FP_NSTATS} int64 values, got {stats.numel()}")
     _check("fp_findpts_stats", lib().fp_findpts_stats(
         mesh, _ptr(pts, torch.float64, "pts"), n, _ptr(code, torch.int32, "code"),
         _ptr(elem, torch.int32, "elem"), _ptr(r, torch.float64, "r"),
@@ -476,6 +484,9 @@ class Mesh:
 
     def set_precision(self, precision: int):
         fp_set_precision(self.handle, precision)
+
+    def set_point_order(self, order: int):
+        fp_set_point_order(self.handle, order)
 
     def find(self, pts, stream=None, stats=None):
         import torch

@@ -20,6 +20,10 @@ int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, 
 
 }  // namespace fp
 
+// Below this many points the counting sort of the cell order costs more
+// than the locality it buys.
+constexpr int64_t kOrderMinPoints = 1 << 14;
+
 static int findpts_impl(fp_mesh m, const double* pts, int64_t n, int32_t* code, int32_t* elem,
                         double* r, double* dist2, uint64_t* stats, void* stream) {
   if (!m || n < 0 || n > INT32_MAX) return FP_EINVAL;
@@ -27,8 +31,27 @@ static int findpts_impl(fp_mesh m, const double* pts, int64_t n, int32_t* code, 
   if (!pts || !code || !elem || !r || !dist2) return FP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   auto* s = reinterpret_cast<unsigned long long*>(stats);
-  if (m->precision == FP_MIXED) return fp::find_mixed(m, pts, n, code, elem, r, dist2, s, st);
-  return fp::find_f64(m, pts, nullptr, n, code, elem, r, dist2, s, st);
+  const bool mixed = m->precision == FP_MIXED;
+  const bool ordered = m->opts.point_order == FP_ORDER_CELL && n >= kOrderMinPoints;
+  // scratch: the mixed path's queue (n entries + counter), then the order
+  const int64_t nq = mixed ? n + 1 : 0;
+  const int64_t ints = nq + (ordered ? fp::cell_order_ints(m, n) : 0);
+  int* scratch = nullptr;
+  if (ints > 0 && cudaMallocAsync((void**)&scratch, sizeof(int) * (size_t)ints, st) != cudaSuccess)
+    return FP_ENOMEM;
+  int* perm = nullptr;
+  int rc = ordered ? fp::cell_order(m, pts, n, scratch + nq, &perm, st) : FP_OK;
+  if (rc == FP_OK) {
+    if (mixed) {
+      rc = cudaMemsetAsync(scratch + n, 0, sizeof(int), st) == cudaSuccess ? FP_OK : FP_ELAUNCH;
+      if (rc == FP_OK)
+        rc = fp::launch_mixed_with_queue(m, pts, perm, n, code, elem, r, dist2, scratch, scratch + n, s, st);
+    } else {
+      rc = fp::find_f64(m, pts, perm, n, code, elem, r, dist2, s, st);
+    }
+  }
+  if (scratch) cudaFreeAsync(scratch, st);
+  return rc;
 }
 
 extern "C" int fp_findpts(fp_mesh m, const double* pts, int64_t n, int32_t* code, int32_t* elem,
@@ -46,5 +69,11 @@ extern "C" int fp_findpts_stats(fp_mesh m, const double* pts, int64_t n, int32_t
 extern "C" int fp_set_precision(fp_mesh m, int precision) {
   if (!m || (precision != FP_F64 && precision != FP_MIXED)) return FP_EINVAL;
   m->precision = precision;
+  return FP_OK;
+}
+
+extern "C" int fp_set_point_order(fp_mesh m, int order) {
+  if (!m || (order != FP_ORDER_GIVEN && order != FP_ORDER_CELL)) return FP_EINVAL;
+  m->opts.point_order = order;
   return FP_OK;
 }

@@ -15,15 +15,15 @@ constexpr int kFindThreads = 128;
 // steps, [3] beta = 1 iterations, [4] FP64 refinement evaluations (mixed),
 // [5] box tests decided in FP64, [6] points handed to the FP64 kernel (mixed).
 struct Counters {
-  unsigned v[7];
+  unsigned v[8];
   __device__ Counters() {
 #pragma unroll
-    for (int i = 0; i < 7; ++i) v[i] = 0;
+    for (int i = 0; i < 8; ++i) v[i] = 0;
   }
   __device__ void flush(unsigned long long* stats) {
     if (!stats) return;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < 8; ++i) {
       unsigned x = v[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -626,7 +626,12 @@ struct BatchWork {
 
 int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
              int* elem, double* r, double* dist2, unsigned long long* stats, cudaStream_t st);
-int find_mixed(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem, double* r,
-               double* dist2, unsigned long long* stats, cudaStream_t st);
+int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
+                            int* elem, double* r, double* dist2, int* queue, int* qcount,
+                            unsigned long long* stats, cudaStream_t st);
+// Cell-grouped point order (order.cu): scratch of cell_order_ints ints;
+// *perm points into it.
+int64_t cell_order_ints(const fp_mesh_s* m, int64_t n);
+int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, int** perm, cudaStream_t st);
 
 }  // namespace fp

@@ -120,6 +120,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
         if (beta && !hess_term_slice<N, D, DR, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r, dx, G, HS)) {
           hess_term<N, D, DR, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r, dx, ts, HS);
         }
+        if (beta) ++cnt.v[3];
         double ds[DR];
         bool used_beta;
         const double mx = newton_step<D, DR>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
@@ -136,7 +137,6 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
             done = true;
           } else {
             ++cnt.v[1];
-            if (beta) ++cnt.v[3];
             etype = E_TRIAL;
             need = true;
           }
@@ -169,6 +169,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
 #pragma unroll
       for (int j = 0; j < DR; ++j) re[j] = (etype == E_TRIAL) ? rn[j] : r[j];
       double xv[D];
+      if (etype != E_RESTORE) ++cnt.v[7];
       eval_xG<N, D, DR, true, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, re, ts, xv, G);
       double Fn = 0.0;
 #pragma unroll

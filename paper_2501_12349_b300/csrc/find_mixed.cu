@@ -36,6 +36,10 @@ constexpr float kBorder32 = 1e-4f; // "clearly outside": distance > kBorder32 * 
 constexpr int kPark = 28;          // run the FP64 refinement with >= kPark lanes parked
 constexpr int kMaxRefine = 4;
 
+// The FP64 kernel that finishes the queued points counts into the second
+// half of the statistics array, so the two precisions' work stays separate.
+inline unsigned long long* fallback_stats(unsigned long long* stats) { return stats ? stats + 8 : nullptr; }
+
 // The mixed-precision lane loop over a source of work (see find_f64.cuh).
 template <int N, int D, int DR, class Work>
 __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B, int* __restrict__ queue,
@@ -145,6 +149,7 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
         float HS[DR][DR];
         if (beta && !hess_term_slice<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, G, HS))
           hess_term<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, ts32, HS);
+        if (beta) ++cnt.v[3];
         float ds[DR];
         bool used_beta;
         const float mx = newton_step<D, DR, float>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
@@ -160,7 +165,6 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
             done = true;
           } else {
             ++cnt.v[1];
-            if (beta) ++cnt.v[3];
             etype = X_TRIAL;
             need = true;
           }
@@ -269,6 +273,7 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
 #pragma unroll
       for (int j = 0; j < DR; ++j) re[j] = (etype == X_TRIAL) ? rn[j] : r[j];
       float xv[D];
+      if (etype != X_REST) ++cnt.v[7];
       eval_xG<N, D, DR, true, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, re, ts32, xv, G);
       float Fn = 0.f;
 #pragma unroll
@@ -305,10 +310,10 @@ constexpr int kMixedCtasPerSm = 3;
 template <int N, int D, int DR>
 __global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
     k_find_mixed(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
-                 int64_t n, int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
-                 double* __restrict__ dist2, int* __restrict__ queue, int* __restrict__ qcount,
-                 unsigned long long* stats) {
-  const SingleWork<D, DR> w{&m, pts, nullptr, n, code, elem, rout, dist2, 5};
+                 const int* __restrict__ pidx, int64_t n, int* __restrict__ code, int* __restrict__ elem,
+                 double* __restrict__ rout, double* __restrict__ dist2, int* __restrict__ queue,
+                 int* __restrict__ qcount, unsigned long long* stats) {
+  const SingleWork<D, DR> w{&m, pts, pidx, n, code, elem, rout, dist2, 5};
   find_mixed_loop<N, D, DR>(w, B, queue, qcount, stats);
 }
 
@@ -323,43 +328,22 @@ __global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
 
 }  // namespace
 
-int find_mixed(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem, double* r,
-               double* dist2, unsigned long long* stats, cudaStream_t st) {
-  int* queue = nullptr;
-  if (cudaMallocAsync((void**)&queue, sizeof(int) * (size_t)(n + 1), st) != cudaSuccess) return FP_ENOMEM;
-  int* qcount = queue + n;
-  int rc = FP_OK;
-  if (cudaMemsetAsync(qcount, 0, sizeof(int), st) != cudaSuccess) rc = FP_ELAUNCH;
-  const DevMesh v = m->view();
-  if (rc == FP_OK)
-    rc = dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
-      constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
-      k_find_mixed<N, D, DR><<<persistent_blocks(n, kMixedCtasPerSm), kFindThreads, 0, st>>>(
-          v, m->basis, pts, n, code, elem, r, dist2, queue, qcount, stats);
-      k_find_f64<N, D, DR><<<persistent_blocks(n, 2), kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount,
-                                                                             code, elem, r, dist2, stats);
-      return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
-    });
-  cudaFreeAsync(queue, st);
-  return rc;
-}
-
 }  // namespace fp
 
 namespace fp {
 
 // The two launches of the mixed path with a caller-provided queue
 // (capacity >= n entries) and zeroed counter; allocates nothing.
-int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem,
-                            double* r, double* dist2, int* queue, int* qcount,
+int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
+                            int* elem, double* r, double* dist2, int* queue, int* qcount,
                             unsigned long long* stats, cudaStream_t st) {
   const DevMesh v = m->view();
   return dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
     k_find_mixed<N, D, DR><<<persistent_blocks(n, kMixedCtasPerSm), kFindThreads, 0, st>>>(
-        v, m->basis, pts, n, code, elem, r, dist2, queue, qcount, stats);
-    k_find_f64<N, D, DR><<<persistent_blocks(n, 2), kFindThreads, 0, st>>>(v, m->basis, pts, queue, n, qcount,
-                                                                           code, elem, r, dist2, stats);
+        v, m->basis, pts, pidx, n, code, elem, r, dist2, queue, qcount, stats);
+    k_find_f64<N, D, DR><<<persistent_blocks(n, 2), kFindThreads, 0, st>>>(
+        v, m->basis, pts, queue, n, qcount, code, elem, r, dist2, fallback_stats(stats));
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
   });
 }
@@ -380,7 +364,7 @@ int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N,
       k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, B, queue, qcount,
                                                                      clog2, stats);
       k_find_f64_batch<NN, D, DR><<<persistent_blocks(total, 2), kFindThreads, 0, st>>>(
-          items, nitems, total, queue, qcount, B, clog2, stats);
+          items, nitems, total, queue, qcount, B, clog2, fallback_stats(stats));
     } else {
       k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, nullptr, nullptr, B,
                                                                    clog2, stats);

@@ -10,12 +10,6 @@
 
 #include "find_common.cuh"
 
-namespace fp {
-int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, int64_t n, int* code, int* elem,
-                            double* r, double* dist2, int* queue, int* qcount,
-                            unsigned long long* stats, cudaStream_t st);
-}
-
 namespace {
 
 // Queue entries [0, FP_NOALLOC_MAX_POINTS) and the counter at the end.
@@ -57,5 +51,5 @@ extern "C" int fp_findpts_mixed_noalloc(fp_mesh m, const double* pts, int64_t n,
   int* qcount = queue + FP_NOALLOC_MAX_POINTS;
   // the counter must start at zero; queue entries are only read below it
   FP_CUDA_TRY(cudaMemsetAsync(qcount, 0, sizeof(int), st));
-  return fp::launch_mixed_with_queue(m, pts, n, code, elem, r, dist2, queue, qcount, nullptr, st);
+  return fp::launch_mixed_with_queue(m, pts, nullptr, n, code, elem, r, dist2, queue, qcount, nullptr, st);
 }

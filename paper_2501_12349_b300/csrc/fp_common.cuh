@@ -89,6 +89,34 @@ __device__ __forceinline__ void record_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// A template so that only the translation units that launch it compile it.
+// Exclusive scan of counts[0..n) into start[0..n], start[n] = total, by one
+// CTA: each thread scans a contiguous chunk.
+template <int kUnused = 0>
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ counts, int64_t n,
+                                               int* __restrict__ start) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x;
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t b = t * chunk, en = b + chunk < n ? b + chunk : n;
+  long long s = 0;
+  for (int64_t i = b; i < en; ++i) s += counts[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    long long v = (t >= o) ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  long long run = part[t] - s;
+  for (int64_t i = b; i < en; ++i) {
+    start[i] = (int)run;
+    run += counts[i];
+  }
+  if (t == (int)blockDim.x - 1) start[n] = (int)part[t];
+}
+
 }  // namespace fp
 
 // The library-owned mesh object behind the fp_mesh handle.

@@ -516,32 +516,6 @@ __global__ void k_grid_scatter(const double* __restrict__ aabb, int64_t NE, Grid
   }
 }
 
-// Exclusive scan of counts[0..n) into start[0..n], start[n] = total, by one
-// CTA: each thread scans a contiguous chunk.
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ counts, int64_t n,
-                                               int* __restrict__ start) {
-  __shared__ long long part[1024];
-  const int t = threadIdx.x;
-  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t b = t * chunk, en = b + chunk < n ? b + chunk : n;
-  long long s = 0;
-  for (int64_t i = b; i < en; ++i) s += counts[i];
-  part[t] = s;
-  __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    long long v = (t >= o) ? part[t - o] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  long long run = part[t] - s;
-  for (int64_t i = b; i < en; ++i) {
-    start[i] = (int)run;
-    run += counts[i];
-  }
-  if (t == (int)blockDim.x - 1) start[n] = (int)part[t];
-}
-
 // Ascending element ids within each cell (insertion sort; lists are short).
 __global__ void k_grid_sort(const int* __restrict__ start, int64_t ncell, int* __restrict__ elems) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
@@ -780,6 +754,7 @@ extern "C" void fp_opts_default(fp_opts* o) {
   o->max_iter = 50;
   o->dist_tol = 1e-10;
   o->precision = FP_F64;
+  o->point_order = FP_ORDER_CELL;
 }
 
 extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int64_t NE,
@@ -797,7 +772,8 @@ extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int6
   if (opts) o = *opts;
   if (o.M == 0) o.M = 2 * N;
   if (o.M < 2 || o.M > kMaxM || !(o.bbox_tol >= 0.0) || o.max_iter < 1 || !(o.newton_tol > 0.0) ||
-      o.n_grid < 0 || (o.precision != FP_F64 && o.precision != FP_MIXED))
+      o.n_grid < 0 || (o.precision != FP_F64 && o.precision != FP_MIXED) ||
+      (o.point_order != FP_ORDER_GIVEN && o.point_order != FP_ORDER_CELL))
     return FP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   fp_mesh_s* m = (fp_mesh_s*)calloc(1, sizeof(fp_mesh_s));

@@ -53,7 +53,7 @@ def compare_eval(field, NE, ne, elem, u_oracle, u_gpu, label=""):
     nc = u_oracle.shape[0]
     f = field.reshape(nc, NE, ne)
     e = np.where(elem >= 0, elem, 0)
-    nodal = np.abs(f[:, e, :]).max(axis=2)  # [nc][n]
+    nodal = np.abs(f).max(axis=2)[:, e]  # [nc][n]
     scale = np.maximum(np.abs(u_oracle), nodal)
     err = np.abs(u_oracle - u_gpu) - U_REL * scale
     assert np.max(err) <= 0, f"{label}: eval mismatch, worst excess {np.max(err):.3e}"

@@ -39,7 +39,7 @@ def test_status_strings_and_defaults(lib):
     assert "invalid" in fp.fp_status_string(-1)
     o = fp.fp_opts_default()
     assert o.bbox_tol == 0.1 and o.M == 0 and o.newton_tol == 1e-10 and o.max_iter == 50
-    assert o.dist_tol == 1e-10 and o.precision == fp.FP_F64
+    assert o.dist_tol == 1e-10 and o.precision == fp.FP_F64 and o.point_order == fp.FP_ORDER_CELL
 
 
 def test_argument_checks_without_device(lib):
@@ -54,3 +54,15 @@ def test_argument_checks_without_device(lib):
     assert lib.fp_eval(None, None, None, None, 0, None, 1, None, None) == fp.FP_EINVAL
     assert lib.fp_free(None) == fp.FP_EINVAL
     assert lib.fp_set_precision(None, 0) == fp.FP_EINVAL
+    assert lib.fp_set_point_order(None, fp.FP_ORDER_CELL) == fp.FP_EINVAL
+
+
+def test_header_constants_match_binding():
+    """Every integer #define FP_* of the header has the same value in the binding."""
+    text = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "findpts.h").read_text(), flags=re.S)
+    seen = 0
+    for name, expr in re.findall(r"^#define (FP_\w+)[ \t]+([-0-9() <]+?)[ \t]*$", text, flags=re.M):
+        if hasattr(fp, name):
+            assert getattr(fp, name) == eval(expr), name
+            seen += 1
+    assert seen >= 15 and fp.FP_NSTATS == 16

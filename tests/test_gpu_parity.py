@@ -218,11 +218,43 @@ def test_stats_counters(fp, torch):
     w = W.hex_config(13, 5000, 1, n=6)
     om = oracle.OracleMesh(w.coords, 3, 3, w.N)
     m = gpu_mesh(fp, torch, w.coords, 3, 3, w.order)
-    st = torch.zeros(8, dtype=torch.int64, device="cuda")
+    st = torch.zeros(fp.FP_NSTATS, dtype=torch.int64, device="cuda")
     m.find(torch.from_numpy(w.pts).cuda(), stats=st)
     gs = to_np(st)
     os_ = np.zeros(8, np.int64)
     om.findpts(w.pts, stats=os_)
     assert gs[0] == os_[0]                       # candidates: exact
     assert abs(gs[1] - os_[1]) <= 0.01 * os_[1]  # iterations: same algorithm
+    m.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("case", ["quad2d_p3", "hex3d_p4", "sphere_p4"])
+def test_point_order_invariance(fp, torch, case, precision):
+    """The cell-grouped traversal (the default, for calls of >= 16384 points)
+    gives bit-identical outputs to the points taken as given, also for points
+    outside the grid and with non-finite coordinates; and it agrees with the
+    oracle."""
+    coords, d, dr, order, h = CASES[case]()
+    om = oracle.OracleMesh(coords, d, dr, order + 1)
+    rng = np.random.default_rng(77)
+    n = 40000
+    if dr == d:
+        pts = rng.uniform(-0.2, 1.2, (n, d))
+    else:
+        pts = surface_points(om, rng, n, h)
+        pts[: n // 50] = rng.uniform(-2, 2, (n // 50, d))
+    pts[5] = np.nan
+    pts[17, 0] = np.inf
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    m.set_precision(fp.FP_MIXED if precision == "mixed" else fp.FP_F64)
+    tp = torch.from_numpy(pts).cuda()
+    a = tuple(to_np(t) for t in m.find(tp))
+    m.set_point_order(fp.FP_ORDER_GIVEN)
+    b = tuple(to_np(t) for t in m.find(tp))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y, equal_nan=True)
+    assert a[0][5] == 2 and a[0][17] == 2
+    compare_find(om.findpts(pts), a, label=f"ordered {precision} {case}", xscale=1.3)
+    assert m.device_status() == 0
     m.close()
