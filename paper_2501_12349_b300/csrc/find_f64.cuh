@@ -15,6 +15,7 @@
 //    back to FP64 only inside the margin, so every decision equals the FP64
 //    one while the divergent part costs almost no FP64 issue slots.
 #pragma once
+#include "beta_warp.cuh"
 #include "find_common.cuh"
 
 namespace fp {
@@ -27,8 +28,11 @@ enum : int { E_INIT = 1, E_TRIAL = 2, E_RESTORE = 3 };
 template <int N, int D, int DR, class Work>
 __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, unsigned long long* stats) {
   constexpr int NN = (DR == 3) ? N * N * N : N * N;
-  __shared__ double s_slab[DR == 3 ? 3 * N * kFindThreads : 1];
+  __shared__ double s_slab[DR == 3 ? 2 * N * kFindThreads : 1];
+  __shared__ double s_hs[beta_entries<DR>() * kFindThreads];
+  __shared__ double s_bscr[(kFindThreads / 32) * kBetaScratch];
   const TSlots<N, double> ts{s_slab};
+  double* const wscr = s_bscr + (threadIdx.x >> 5) * kBetaScratch;
   __shared__ unsigned long long s_next;
   if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
@@ -116,11 +120,11 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
         done = true;
       } else {
         const bool beta = (l > 0) && at_bound<DR>(r);
-        double HS[DR][DR];
-        if (beta && !hess_term_slice<N, D, DR, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r, dx, G, HS)) {
-          hess_term<N, D, DR, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r, dx, ts, HS);
+        double HS[DR][DR] = {};
+        if (beta) {
+          beta_load<DR, double>(s_hs, HS);  // computed by the warp after the last evaluation
+          ++cnt.v[3];
         }
-        if (beta) ++cnt.v[3];
         double ds[DR];
         bool used_beta;
         const double mx = newton_step<D, DR>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
@@ -196,6 +200,13 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
         F = Fn;
         mode = M_NEWTON;
       }
+    }
+    // ---- warp-uniform beta term for the next Newton step -----------------
+    {
+      const bool want = need && mode == M_NEWTON && l > 0 && at_bound<DR>(r);
+      const BetaReq bq = beta_request<N, D, DR, double>(want, r, dx, G);
+      if (__any_sync(0xffffffffu, bq.kind != BETA_NONE))
+        beta_warp<N, D, DR, double>(bq, mp->coords + (int64_t)e * NN, mp->cstride, r, dx, B, wscr, s_hs);
     }
   }
   cnt.flush(stats);
