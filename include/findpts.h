@@ -209,8 +209,9 @@ int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_item* items, i
 int fp_batch_run(fp_batch b, void* stream);
 
 /* The launch shape autotuner: for every element shape of the plan, times the
- * shape's launches for CTAs per SM in {1, 2} (FP_F64) or {2, 3} (FP_MIXED) and
- * points per CTA chunk in {32, 128, 512} on the plan's own data (best of two timed runs each), keeps
+ * shape's launches for CTAs per SM (the kernel's register-limited maximum
+ * and one fewer: {2, 3} for FP_MIXED and for FP_F64 up to order 5, {1, 2}
+ * for FP_F64 at orders 6 and 7) and points per CTA chunk in {32, 128, 512} on the plan's own data (best of two timed runs each), keeps
  * the fastest, records it for later plans and re-captures the graph.
  * Overwrites the plan's outputs.  Synchronous. */
 int fp_batch_autotune(fp_batch b, void* stream);

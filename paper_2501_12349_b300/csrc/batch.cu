@@ -75,7 +75,7 @@ int launch_eval_class(const BatchItem* items, int nitems, int64_t total, int N, 
 }
 
 struct Tuning {
-  int ctas_per_sm = 2;  // default; fp_batch_autotune may pick 1-3
+  int ctas_per_sm = 0;  // 0: the kernel's own (3 mixed; f64_ctas(N) FP64)
   int clog2 = 5;
   float ms = -1.f;  // measured time of the chosen shape, -1 if untuned
 };
@@ -293,8 +293,6 @@ extern "C" int fp_batch_autotune(fp_batch b, void* stream) {
   using namespace fp;
   if (!b) return FP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  // CTAs per SM: the FP64 kernel holds 2 per SM, the mixed one 3
-  const int ctas[2] = {b->precision == FP_MIXED ? 2 : 1, b->precision == FP_MIXED ? 3 : 2};
   const int clogs[3] = {5, 7, 9};
   cudaEvent_t e0, e1;
   FP_CUDA_TRY(cudaEventCreate(&e0));
@@ -303,6 +301,9 @@ extern "C" int fp_batch_autotune(fp_batch b, void* stream) {
   for (auto& c : b->classes) {
     if (c.total == 0 || rc != FP_OK) continue;
     Tuning best;
+    // CTAs per SM: the kernel's register-limited maximum and one fewer
+    const int cmax = b->precision == FP_MIXED ? 3 : f64_ctas(c.N);
+    const int ctas[2] = {cmax - 1, cmax};
     for (int a = 0; a < 2 && rc == FP_OK; ++a)
       for (int k = 0; k < 3 && rc == FP_OK; ++k) {
         Tuning t;
@@ -342,7 +343,8 @@ extern "C" int fp_batch_describe(fp_batch b, int i, fp_batch_class_info* info) {
   info->dr = c.dr;
   info->n_items = (int)c.items.size();
   info->n_points = c.total;
-  info->ctas_per_sm = c.tune.ctas_per_sm;
+  info->ctas_per_sm = c.tune.ctas_per_sm > 0 ? c.tune.ctas_per_sm
+                                             : (b->precision == FP_MIXED ? 3 : fp::f64_ctas(c.N));
   info->chunk_points = 1 << c.tune.clog2;
   info->tuned_ms = c.tune.ms;
   return FP_OK;

@@ -32,6 +32,10 @@ struct Counters {
   }
 };
 
+// CTAs of kFindThreads per SM that the FP64 find kernel is compiled for:
+// its registers fit three per SM up to N = 6 and two above.
+__host__ __device__ constexpr int f64_ctas(int N) { return N <= 6 ? 3 : 2; }
+
 inline int sm_count() {
   static int n = 0;
   if (n == 0) {

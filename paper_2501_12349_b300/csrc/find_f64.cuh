@@ -213,7 +213,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
 }
 
 template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, 2)
+__global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
     k_find_f64(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
                const int* __restrict__ pidx, int64_t n, const int* __restrict__ n_dev,
                int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kFindThreads, 2)
 // Every item of a batch (one element shape) in one persistent launch; gidx /
 // n_dev optionally restrict it to a device-produced list of global indices.
 template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, 2)
+__global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
     k_find_f64_batch(const BatchItem* __restrict__ items, int nitems, int64_t total,
                      const int* __restrict__ gidx, const int* __restrict__ n_dev, const BasisTab B,
                      int clog2, unsigned long long* stats) {

@@ -46,7 +46,10 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
                                                 int* __restrict__ qcount, unsigned long long* stats) {
   constexpr int NN = (DR == 3) ? N * N * N : N * N;
   __shared__ double s_slab64[DR == 3 ? 2 * N * kFindThreads : 1];
-  __shared__ float s_slab32[DR == 3 ? 3 * N * kFindThreads : 1];
+  __shared__ float s_slab32[DR == 3 ? 2 * N * kFindThreads : 1];
+  __shared__ float s_hs[beta_entries<DR>() * kFindThreads];
+  __shared__ float s_bscr[(kFindThreads / 32) * kBetaScratch];
+  float* const wscr = s_bscr + (threadIdx.x >> 5) * kBetaScratch;
   const TSlots<N, double> ts64{s_slab64};
   const TSlots<N, float> ts32{s_slab32};
   __shared__ unsigned long long s_next;
@@ -146,10 +149,11 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
         done = true;
       } else {
         const bool beta = (l > 0) && at_bound<DR>(r);
-        float HS[DR][DR];
-        if (beta && !hess_term_slice<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, G, HS))
-          hess_term<N, D, DR, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, r, dx, ts32, HS);
-        if (beta) ++cnt.v[3];
+        float HS[DR][DR] = {};
+        if (beta) {
+          beta_load<DR, float>(s_hs, HS);  // computed by the warp after the last evaluation
+          ++cnt.v[3];
+        }
         float ds[DR];
         bool used_beta;
         const float mx = newton_step<D, DR, float>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
@@ -301,6 +305,13 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
         mode = X_NEWTON;
       }
     }
+    // ---- warp-uniform beta term for the next FP32 Newton step ------------
+    {
+      const bool want = need && mode == X_NEWTON && l > 0 && at_bound<DR>(r);
+      const BetaReq bq = beta_request<N, D, DR, float>(want, r, dx, G);
+      if (__any_sync(0xffffffffu, bq.kind != BETA_NONE))
+        beta_warp<N, D, DR, float>(bq, mp->coords32 + (int64_t)e * NN, mp->cstride, r, dx, B, wscr, s_hs);
+    }
   }
   cnt.flush(stats);
 }
@@ -342,7 +353,7 @@ int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pi
     constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
     k_find_mixed<N, D, DR><<<persistent_blocks(n, kMixedCtasPerSm), kFindThreads, 0, st>>>(
         v, m->basis, pts, pidx, n, code, elem, r, dist2, queue, qcount, stats);
-    k_find_f64<N, D, DR><<<persistent_blocks(n, 2), kFindThreads, 0, st>>>(
+    k_find_f64<N, D, DR><<<persistent_blocks(n, f64_ctas(N)), kFindThreads, 0, st>>>(
         v, m->basis, pts, queue, n, qcount, code, elem, r, dist2, fallback_stats(stats));
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
   });
@@ -359,11 +370,12 @@ int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N,
                        int* qcount, unsigned long long* stats, cudaStream_t st) {
   return dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int NN = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
+    if (ctas_per_sm <= 0) ctas_per_sm = precision == FP_MIXED ? kMixedCtasPerSm : f64_ctas(NN);
     const int blocks = persistent_blocks(total, ctas_per_sm);
     if (precision == FP_MIXED) {
       k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, B, queue, qcount,
                                                                      clog2, stats);
-      k_find_f64_batch<NN, D, DR><<<persistent_blocks(total, 2), kFindThreads, 0, st>>>(
+      k_find_f64_batch<NN, D, DR><<<persistent_blocks(total, f64_ctas(NN)), kFindThreads, 0, st>>>(
           items, nitems, total, queue, qcount, B, clog2, fallback_stats(stats));
     } else {
       k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, nullptr, nullptr, B,

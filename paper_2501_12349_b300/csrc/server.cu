@@ -398,7 +398,7 @@ int launch_tick(fp_server_s* s, TickSlot& t) {
     int* qq = t.queue + off;
     if (s->opts.precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qq + total, 0, sizeof(int), t.st));
     FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision,
-                              s->opts.precision == FP_MIXED ? 3 : 2, 5, qq, qq + total, nullptr, t.st));
+                              0, 5, qq, qq + total, nullptr, t.st));
     FP_TRY(dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
       constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
       (void)Dc;
