@@ -173,6 +173,18 @@ int fp_findpts_mixed_noalloc(fp_mesh m, const double* pts_dev, int64_t n, int32_
 int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
             int64_t n, const double* field_dev, int nc, double* out, void* stream);
 
+/* Interpolate a field of another order (Sec. 2, after Eq. u_tensor: the
+ * solution's order N~ - 1 often differs from the coordinates' order N - 1).
+ * field_dev is [nc][NE][(field_order+1)^dr] FP64 on the GLL nodes of
+ * field_order + 1 points per direction, in the node layout of the
+ * coordinates; code, elem, r come from fp_findpts on the same mesh and
+ * out[c][p] as fp_eval.  field_order == the mesh's order is fp_eval.
+ * Errors: FP_EINVAL; FP_EUNSUPPORTED unless 1 <= field_order <= 7;
+ * FP_ELAUNCH. */
+int fp_eval_order(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
+                  int64_t n, const double* field, int field_order, int nc, double* out,
+                  void* stream);
+
 /* ---- many meshes in one graph launch ---------------------------------------
  * A batch plan runs find (and optionally eval) for many (mesh, point set)
  * items at once: items are grouped by element shape (N, d, dr); per shape one

@@ -217,13 +217,16 @@ class OracleMesh:
                                        _p(pts), n, _p(count, _I32), _p(first, _I32)) == 0
         return count, first
 
-    def eval(self, field, code, elem, r):
+    def eval(self, field, code, elem, r, field_N=None):
+        """Eq. u_tensor: the field on field_N GLL nodes per direction (the
+        mesh's N unless given; Sec. 2 allows the two to differ)."""
+        Nf = self.N if field_N is None else int(field_N)
         field = _f64(field)
-        nc = field.size // (self.NE * self.N ** self.dr)
+        nc = field.size // (self.NE * Nf ** self.dr)
         code, elem, r = _i32(code), _i32(elem), _f64(r)
         n = code.shape[0]
         out = np.zeros((nc, n))
-        assert lib().or_eval(_p(field), nc, self.dr, self.N, self.NE, _p(code, _I32), _p(elem, _I32),
+        assert lib().or_eval(_p(field), nc, self.dr, Nf, self.NE, _p(code, _I32), _p(elem, _I32),
                              _p(r), n, _p(out)) == 0
         return out
 

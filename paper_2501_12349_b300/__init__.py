@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
             "fp_findpts": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _int),
             "fp_findpts_stats": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fp_eval": ([_vp, _vp, _vp, _vp, _i64, _vp, _int, _vp, _vp], _int),
+            "fp_eval_order": ([_vp, _vp, _vp, _vp, _i64, _vp, _int, _int, _vp, _vp], _int),
             "fp_get_info": ([_vp, ctypes.POINTER(FpMeshInfo)], _int),
             "fp_get_boxes": ([_vp, _vp, _vp, _vp, _vp], _int),
             "fp_get_grid": ([_vp, _vp, _vp, _vp], _int),
@@ -165,6 +166,15 @@ def fp_eval(mesh, code, elem, r, field, nc: int, out, stream=None) -> None:
     _check("fp_eval", lib().fp_eval(
         mesh, _ptr(code, torch.int32, "code"), _ptr(elem, torch.int32, "elem"),
         _ptr(r, torch.float64, "r"), n, _ptr(field, torch.float64, "field"), int(nc),
+        _ptr(out, torch.float64, "out"), _stream(stream)))
+
+
+def fp_eval_order(mesh, code, elem, r, field, field_order: int, nc: int, out, stream=None) -> None:
+    import torch
+    n = code.shape[0]
+    _check("fp_eval_order", lib().fp_eval_order(
+        mesh, _ptr(code, torch.int32, "code"), _ptr(elem, torch.int32, "elem"),
+        _ptr(r, torch.float64, "r"), n, _ptr(field, torch.float64, "field"), int(field_order), int(nc),
         _ptr(out, torch.float64, "out"), _stream(stream)))
 
 
@@ -502,11 +512,17 @@ class Mesh:
             fp_findpts_stats(self.handle, pts, code, elem, r, dist2, stats, stream)
         return code, elem, r, dist2
 
-    def eval(self, code, elem, r, field, stream=None):
+    def eval(self, code, elem, r, field, stream=None, order=None):
+        """Interpolates field ([nc][NE][(order+1)^dr]; order defaults to the
+        mesh's) at the find output (code, elem, r)."""
         import torch
-        nc = field.numel() // (self.NE * self.N ** self.dr)
+        Nf = self.N if order is None else order + 1
+        nc = field.numel() // (self.NE * Nf ** self.dr)
         out = torch.empty((nc, code.shape[0]), dtype=torch.float64, device=code.device)
-        fp_eval(self.handle, code, elem, r, field, nc, out, stream)
+        if order is None:
+            fp_eval(self.handle, code, elem, r, field, nc, out, stream)
+        else:
+            fp_eval_order(self.handle, code, elem, r, field, order, nc, out, stream)
         return out
 
     def info(self) -> FpMeshInfo:

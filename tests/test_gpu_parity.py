@@ -258,3 +258,55 @@ def test_point_order_invariance(fp, torch, case, precision):
     compare_find(om.findpts(pts), a, label=f"ordered {precision} {case}", xscale=1.3)
     assert m.device_status() == 0
     m.close()
+
+
+@pytest.mark.parametrize("case,field_order", [("hex3d_p4", 2), ("hex3d_p4", 7), ("quad2d_p3", 5),
+                                              ("sphere_p4", 1), ("torus_p3", 6)])
+def test_eval_field_order(fp, torch, case, field_order):
+    """fp_eval_order (a field of another order than the mesh, Sec. 2 after
+    Eq. u_tensor) against the oracle's interpolation at the oracle's find
+    output, 3 components; random nodal values."""
+    coords, d, dr, order, h = CASES[case]()
+    N = order + 1
+    Nf = field_order + 1
+    om = oracle.OracleMesh(coords, d, dr, N)
+    rng = np.random.default_rng(13)
+    if dr == d:
+        pts = rng.uniform(-0.05, 1.05, (20000, d))
+    else:
+        pts = surface_points(om, rng, 20000, h)
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    g = gpu_find(torch, m, pts)
+    o = om.findpts(pts)
+    compare_find(o, g, label=case)
+    fld = rng.uniform(-1, 1, (3, om.NE * Nf ** dr))
+    # the oracle's find output as input: random nodal values make the field
+    # discontinuous across elements, so tied BORDER answers would differ
+    code, elem, r = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in o[:3])
+    u = to_np(m.eval(code, elem, r, torch.from_numpy(fld).cuda(), order=field_order))
+    uo = om.eval(fld, *o[:3], field_N=Nf)
+    compare_eval(fld, om.NE, Nf ** dr, o[1], uo, u, f"{case} field order {field_order}")
+    assert m.device_status() == 0
+    m.close()
+
+
+def test_many_fields_one_find(fp, torch):
+    """Several fields evaluated from one find output (Sec. 3.3: Find once,
+    interpolate every field): one call per field equals one call with all
+    fields as components, bit for bit, and matches the oracle."""
+    coords, d, dr, order, h = CASES["hex3d_p4"]()
+    om = oracle.OracleMesh(coords, d, dr, order + 1)
+    rng = np.random.default_rng(14)
+    pts = rng.uniform(0, 1, (30000, 3))
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    code, elem, r, d2 = m.find(torch.from_numpy(pts).cuda())
+    fields = [rng.uniform(-1, 1, (1, om.NE * (order + 1) ** 3)) for _ in range(4)]
+    sep = [to_np(m.eval(code, elem, r, torch.from_numpy(f).cuda())) for f in fields]
+    allf = to_np(m.eval(code, elem, r, torch.from_numpy(np.concatenate(fields)).cuda()))
+    assert np.array_equal(np.concatenate(sep), allf)
+    o = om.findpts(pts)
+    oc, oe, orr = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in o[:3])
+    uo = to_np(m.eval(oc, oe, orr, torch.from_numpy(np.concatenate(fields)).cuda()))
+    compare_eval(np.concatenate(fields), om.NE, (order + 1) ** 3, o[1], om.eval(np.concatenate(fields), *o[:3]),
+                 uo, "many fields")
+    m.close()

@@ -298,3 +298,47 @@ def test_nonfinite_points_not_found(config1_oracle):
     bad = np.array([[np.nan, 0.5], [0.5, np.inf], [-np.inf, -np.inf]])
     code, elem, r, dist2 = m.findpts(bad)
     assert np.all(code == 2) and np.all(elem == -1)
+
+
+@pytest.mark.parametrize("dr,N,Nf", [(3, 5, 3), (3, 3, 6), (3, 4, 4), (2, 2, 8), (2, 6, 2), (2, 4, 7)])
+def test_eval_field_order_differs(dr, N, Nf):
+    """A field of N~ nodes per direction (Sec. 2, after Eq. u_tensor: N~ may
+    differ from the mesh's N): values P(zeta~_i, zeta~_j[, zeta~_k]) of a
+    polynomial P of degree <= N~-1 in each reference variable are
+    interpolated exactly at any r, whatever N is; a polynomial of degree N~
+    in one variable is not (so the N~-point basis is the one used)."""
+    d = 3
+    if dr == 3:
+        coords = W.hex_mesh(2, N - 1, 0.2)
+    else:
+        coords = W.cubed_sphere(1, N - 1)
+    m = oracle.OracleMesh(coords, d, dr, N)
+    rng = np.random.default_rng(100 + 10 * N + Nf)
+    z = W.gll_points(Nf)
+    grids = np.meshgrid(*([z] * dr), indexing="ij")  # grids[j][i0, i1, (i2)]
+    nodes = [g.transpose(*reversed(range(dr))).reshape(-1) for g in grids]  # r_j of node q, r fastest
+
+    def poly(c, pts):
+        v = np.zeros(pts[0].shape)
+        for idx in np.ndindex(*c.shape):
+            t = c[idx]
+            for j in range(dr):
+                t = t * pts[j] ** idx[j]
+            v = v + t
+        return v
+
+    c = rng.uniform(-1, 1, (Nf,) * dr)
+    scale = 1.0 + np.arange(m.NE)[:, None]
+    field = (scale * poly(c, nodes)[None, :])[None]
+    n = 400
+    elem = rng.integers(0, m.NE, n).astype(np.int32)
+    r = rng.uniform(-1, 1, (n, dr))
+    code = np.zeros(n, np.int32)
+    out = m.eval(field, code, elem, r, field_N=Nf)[0]
+    exact = (1.0 + elem) * poly(c, list(r.T))
+    np.testing.assert_allclose(out, exact, atol=1e-12 * np.abs(exact).max())
+    c2 = np.zeros((Nf + 1,) * dr)
+    c2[(Nf,) + (0,) * (dr - 1)] = 1.0  # r^N~
+    field2 = np.tile(poly(c2, nodes), (m.NE, 1))[None]
+    out2 = m.eval(field2, code, elem, r, field_N=Nf)[0]
+    assert np.max(np.abs(out2 - r[:, 0] ** Nf)) > 1e-3
