@@ -291,6 +291,9 @@ int or_bound_2d(int N, int M, const double* u, double* lo, double* hi) {
   return 0;
 }
 
+/* N^dr: nodes of a tensor-product element (lines, quads, hexes). */
+static int nodes_per_elem(int N, int dr) { return dr == 1 ? N : (dr == 2 ? N * N : N * N * N); }
+
 /* ------------------------------------------------------------------------ */
 /* Direct evaluation of the element map, Eq. x / x_tensor: x_c(r) and, when
  * requested, G[c][j] = dx_c/dr_j (Eq. jacobian) and the second derivatives
@@ -299,7 +302,7 @@ static void eval_map(const double* coords, int d, int dr, int N, int64_t NE, int
                      const double* z, const double* r, double* x, double* G, double* S) {
   double phi[3][OR_MAXN], dphi[3][OR_MAXN], d2phi[3][OR_MAXN];
   for (int j = 0; j < dr; ++j) or_lagrange(N, z, r[j], phi[j], dphi[j], d2phi[j]);
-  const int ne = (dr == 3) ? N * N * N : N * N;
+  const int ne = nodes_per_elem(N, dr);
   for (int c = 0; c < d; ++c) {
     x[c] = 0.0;
     if (G)
@@ -370,6 +373,13 @@ static double inv_small(int d, const double* A, double* Ai) {
 static void element_bounds(const double* u, int d, int dr, int N, int M, double* lo, double* hi) {
   double L = INFINITY, H = -INFINITY, l, h;
   double piece[OR_MAXN * OR_MAXN];
+  if (dr == 1) {
+    /* line elements (Sec. 2, Eq. x_tensor_surf): the element is a 1D function */
+    or_bound_1d(N, M, u, &l, &h);
+    *lo = l;
+    *hi = h;
+    return;
+  }
   if (dr == 2 && d == 3) {
     or_bound_2d(N, M, u, &l, &h);
     *lo = l;
@@ -481,19 +491,59 @@ static void surface_frame(const double* Jc /* 3x2 */, double* R) {
     }
 }
 
+/* Orientation frame of a line element, Sec. 4.2: the Rodrigues rotation R
+ * that takes the unit tangent t/|t| at r = 0 to the x axis (2D: the plane
+ * rotation by minus the tangent's angle; 3D: rotation about t x e1 by the
+ * angle between t and e1; a tangent along -e1 turns by pi about e3).        */
+static void line_frame(int d, const double* t, double* R) {
+  double nt = 0.0;
+  for (int c = 0; c < d; ++c) nt += t[c] * t[c];
+  nt = sqrt(nt);
+  double u[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < d; ++c) u[c] = t[c] / nt;
+  if (d == 2) {
+    R[0] = u[0];
+    R[1] = u[1];
+    R[2] = -u[1];
+    R[3] = u[0];
+    return;
+  }
+  /* axis k = u x e1 = (0, u2, -u1), sin = |k|, cos = u . e1 */
+  double v[3] = {0.0, u[2], -u[1]};
+  double s = sqrt(v[1] * v[1] + v[2] * v[2]), co = u[0];
+  if (s == 0.0) {
+    for (int i = 0; i < 9; ++i) R[i] = 0.0;
+    R[0] = (co > 0) ? 1.0 : -1.0;
+    R[4] = (co > 0) ? 1.0 : -1.0;
+    R[8] = 1.0;
+    return;
+  }
+  double k[3] = {0.0, v[1] / s, v[2] / s};
+  double K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double q = 0;
+      for (int m = 0; m < 3; ++m) q += K[i * 3 + m] * K[m * 3 + j];
+      K2[i * 3 + j] = q;
+    }
+  for (int i = 0; i < 9; ++i) R[i] = ((i % 4) == 0 ? 1.0 : 0.0) + s * K[i] + (1.0 - co) * K2[i];
+}
+
 /* Secs. 3.1.1-3.1.2 and 4.1-4.2: the expanded AABB and OBB of every element.
  * AABB: bounds of each coordinate function (element_bounds), expanded.
  * OBB: x_c = x(r=0), J_c = G(r=0); the nodes are mapped to the frame
  * x~ = T (x - x_c) with T = J_c^{-1} (volumes, Eq. OBB_transformation) or
- * T = R (surfaces); the AABB of x~ (centre m, expanded half-widths hw) is
+ * T = R (surface quads: R2 R1; lines: the Rodrigues rotation); the AABB of x~ (centre m, expanded half-widths hw) is
  * mapped back: OBB centre x_c + T^{-1} m (the paper's x_c + J_c x_c-breve),
  * and the stored matrix A = diag(1/hw) T is J-acute^{-1}, so the test of
  * Eq. OBB_test is |A (x* - centre)|_inf <= 1.                              */
 int or_element_boxes(const double* coords, int d, int dr, int N, int64_t NE, double tol,
                      int M, double* aabb, double* obb_c, double* obb_A) {
-  if (!((d == 2 && dr == 2) || (d == 3 && dr == 3) || (d == 3 && dr == 2))) return -1;
+  if (!((d == 2 && dr == 2) || (d == 3 && dr == 3) || (d == 3 && dr == 2) || (dr == 1 && (d == 2 || d == 3))))
+    return -1;
   if (N < 2 || N > OR_MAXN || M < 2 || M > OR_MAXM) return -1;
-  const int ne = (dr == 3) ? N * N * N : N * N;
+  const int ne = nodes_per_elem(N, dr);
   double z[OR_MAXN];
   or_gll_nodes(N, z);
   int err = 0;
@@ -519,8 +569,10 @@ int or_element_boxes(const double* coords, int d, int dr, int N, int64_t NE, dou
 #pragma omp atomic write
         err = 1;
       }
-    } else {
+    } else if (dr == 2) {
       surface_frame(Jc, T);
+    } else {
+      line_frame(d, Jc, T); /* Jc is the d x 1 tangent */
     }
     inv_small(d, T, Ti);
     double* ut = (double*)malloc(sizeof(double) * ne * d);
@@ -614,7 +666,7 @@ static int chol_solve_free(int dr, int nf, const int* fr, const double* H, const
 static int newton_elem(const double* coords, int d, int dr, int N, int64_t NE, int64_t e,
                        const double* z, const double* xs, double xscale, double tol, int max_iter,
                        double* r, double* dist2, int64_t* st) {
-  const int ne = (dr == 3) ? N * N * N : N * N;
+  const int ne = nodes_per_elem(N, dr);
   /* initial guess: closest node */
   double best = INFINITY;
   int nbest = 0;
@@ -784,7 +836,7 @@ static double aabb_scale(int d, const double* box) {
 /* the expanded AABB of one element (as in or_element_boxes) */
 static void one_aabb(const double* coords, int d, int dr, int N, int64_t NE, int64_t e,
                      double tol, int M, double* box) {
-  const int ne = (dr == 3) ? N * N * N : N * N;
+  const int ne = nodes_per_elem(N, dr);
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, mid[3], hw[3];
   double* u = (double*)malloc(sizeof(double) * ne);
   for (int c = 0; c < d; ++c) {
@@ -945,7 +997,7 @@ int or_eval(const double* field, int nc, int dr, int N, int64_t NE, const int32_
             const int32_t* elem, const double* r, int64_t n, double* out) {
   double z[OR_MAXN];
   if (or_gll_nodes(N, z)) return -1;
-  const int ne = (dr == 3) ? N * N * N : N * N;
+  const int ne = nodes_per_elem(N, dr);
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < n; ++p) {
     if (code[p] == 2 || elem[p] < 0 || elem[p] >= NE) {

@@ -8,6 +8,8 @@
  * trust-region Newton (Sec. 3.2.1), candidate selection (Sec. 3.2) and
  * interpolation (Sec. 3.3).  Candidates come from a brute-force box test over
  * every element (no grid); every basis sum is the direct O(N^dr) sum.
+ * Element shapes (d, dr): quads (2,2), hexes (3,3), surface quads (3,2) and
+ * line elements (2,1), (3,1) (Sec. 2, Eq. x_tensor_surf; Sec. 4.2).
  *
  * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
  * may load this library.  It shares no code with the CUDA library.

@@ -133,6 +133,77 @@ def torus(nu: int, nv: int, order: int, R: float = 1.0, r: float = 0.3) -> np.nd
     return np.ascontiguousarray(np.stack([X, Y, Z]))
 
 
+def circle_lines(n: int, order: int, radius: float = 1.0, centre=(0.0, 0.0)) -> np.ndarray:
+    """n line elements on a circle in 2D, nodes at the GLL points of each
+    element's angle interval (every node exactly on the circle): [2][n][N]."""
+    N = order + 1
+    z = gll_points(N)
+    th = (np.arange(n)[:, None] + 0.5 * (1 + z[None, :])) * (2 * np.pi / n)
+    return np.ascontiguousarray(np.stack([centre[0] + radius * np.cos(th), centre[1] + radius * np.sin(th)]))
+
+
+def helix_lines(n: int, order: int, turns: float = 2.0, radius: float = 0.5, pitch: float = 0.25) -> np.ndarray:
+    """n line elements along a helix in 3D (nodes on the helix): [3][n][N]."""
+    N = order + 1
+    z = gll_points(N)
+    th = (np.arange(n)[:, None] + 0.5 * (1 + z[None, :])) * (2 * np.pi * turns / n)
+    return np.ascontiguousarray(np.stack([radius * np.cos(th), radius * np.sin(th), pitch * th / (2 * np.pi)]))
+
+
+def segment_lines(n: int, order: int, xa, xb) -> np.ndarray:
+    """n straight (affine) line elements splitting the segment xa -> xb."""
+    N = order + 1
+    z = gll_points(N)
+    t = (np.arange(n)[:, None] + 0.5 * (1 + z[None, :])) / n
+    xa, xb = np.asarray(xa, float), np.asarray(xb, float)
+    return np.ascontiguousarray(np.stack([xa[c] + t * (xb[c] - xa[c]) for c in range(len(xa))]))
+
+
+def star_lines(n: int, order: int, a: float = 0.15, k: int = 5) -> np.ndarray:
+    """n line elements on the closed curve rho(theta) = 1 + a cos(k theta) in
+    2D (a curved boundary), nodes at the GLL points of each theta interval."""
+    N = order + 1
+    z = gll_points(N)
+    th = (np.arange(n)[:, None] + 0.5 * (1 + z[None, :])) * (2 * np.pi / n)
+    rho = 1.0 + a * np.cos(k * th)
+    return np.ascontiguousarray(np.stack([rho * np.cos(th), rho * np.sin(th)]))
+
+
+def projection_points(coords: np.ndarray, rng: np.random.Generator, tangential: float = 0.3,
+                      normal: float = 0.01) -> np.ndarray:
+    """Closest-point projection workload (the tangential relaxation of the
+    paper's r-adaptivity example): every node of a 2D line mesh moved along
+    the curve's tangent by up to +-tangential h and off it by up to
+    +-normal h (h = the element's chord), as a mesh optimiser would move
+    boundary nodes.  Returns points [NE*N][2]."""
+    d, NE, N = coords.shape
+    h = np.linalg.norm(coords[:, :, -1] - coords[:, :, 0], axis=0)  # [NE]
+    tan = np.gradient(coords, axis=2)
+    tan = tan / np.linalg.norm(tan, axis=0, keepdims=True)
+    nrm = np.stack([-tan[1], tan[0]])
+    st = rng.uniform(-tangential, tangential, (NE, N)) * h[:, None]
+    sn = rng.uniform(-normal, normal, (NE, N)) * h[:, None]
+    x = coords + st[None] * tan + sn[None] * nrm
+    return np.ascontiguousarray(x.reshape(d, -1).T)
+
+
+def boundary_lines(quad_coords: np.ndarray, n: int) -> np.ndarray:
+    """The boundary of an n x n quad mesh of [0,1]^2 (node layout i + N j,
+    elements row by row) as 4n line elements: [2][4n][N]."""
+    N = int(round(np.sqrt(quad_coords.shape[2])))
+    X = quad_coords.reshape(2, n, n, N, N)  # [c][ey][ex][j][i]
+    edges = []
+    for ex in range(n):
+        edges.append(X[:, 0, ex, 0, :])            # bottom, i along +x
+    for ey in range(n):
+        edges.append(X[:, ey, n - 1, :, N - 1])    # right, j along +y
+    for ex in reversed(range(n)):
+        edges.append(X[:, n - 1, ex, N - 1, ::-1])  # top, towards -x
+    for ey in reversed(range(n)):
+        edges.append(X[:, ey, 0, ::-1, 0])         # left, towards -y
+    return np.ascontiguousarray(np.stack(edges, axis=1))
+
+
 # --------------------------------------------------------------------------
 # fields and points
 

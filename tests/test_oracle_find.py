@@ -300,7 +300,8 @@ def test_nonfinite_points_not_found(config1_oracle):
     assert np.all(code == 2) and np.all(elem == -1)
 
 
-@pytest.mark.parametrize("dr,N,Nf", [(3, 5, 3), (3, 3, 6), (3, 4, 4), (2, 2, 8), (2, 6, 2), (2, 4, 7)])
+@pytest.mark.parametrize("dr,N,Nf", [(3, 5, 3), (3, 3, 6), (3, 4, 4), (2, 2, 8), (2, 6, 2), (2, 4, 7),
+                                     (1, 4, 3), (1, 3, 8)])
 def test_eval_field_order_differs(dr, N, Nf):
     """A field of N~ nodes per direction (Sec. 2, after Eq. u_tensor: N~ may
     differ from the mesh's N): values P(zeta~_i, zeta~_j[, zeta~_k]) of a
@@ -310,8 +311,10 @@ def test_eval_field_order_differs(dr, N, Nf):
     d = 3
     if dr == 3:
         coords = W.hex_mesh(2, N - 1, 0.2)
-    else:
+    elif dr == 2:
         coords = W.cubed_sphere(1, N - 1)
+    else:
+        coords = W.helix_lines(5, N - 1)
     m = oracle.OracleMesh(coords, d, dr, N)
     rng = np.random.default_rng(100 + 10 * N + Nf)
     z = W.gll_points(Nf)
@@ -342,3 +345,120 @@ def test_eval_field_order_differs(dr, N, Nf):
     field2 = np.tile(poly(c2, nodes), (m.NE, 1))[None]
     out2 = m.eval(field2, code, elem, r, field_N=Nf)[0]
     assert np.max(np.abs(out2 - r[:, 0] ** Nf)) > 1e-3
+
+
+# ---- line elements (Sec. 2, Eq. x_tensor_surf; Sec. 4.2 Rodrigues frame) ----
+
+LINES = {
+    "circle2d": lambda: (W.circle_lines(12, 4), 2, 5),
+    "star2d": lambda: (W.star_lines(24, 3), 2, 4),
+    "helix3d": lambda: (W.helix_lines(16, 5), 3, 6),
+    "segment3d": lambda: (W.segment_lines(5, 3, (0.1, -0.2, 0.3), (0.9, 0.5, -0.4)), 3, 4),
+}
+
+
+@pytest.mark.parametrize("name", list(LINES))
+def test_line_boxes_contain_samples(name):
+    """Every expanded AABB and OBB contains dense samples of its curved line
+    element (Secs. 3.1.1-3.1.2 with the line bounds and frame of Sec. 4)."""
+    coords, d, N = LINES[name]()
+    m = oracle.OracleMesh(coords, d, 1, N)
+    rs = np.linspace(-1, 1, 401)
+    for e in range(m.NE):
+        x = m.forward_map(np.full(rs.size, e, np.int32), rs[:, None])
+        lo, hi = m.aabb[e, :d], m.aabb[e, d:]
+        assert np.all(x >= lo - 1e-14) and np.all(x <= hi + 1e-14)
+        y = (x - m.obb_c[e]) @ m.obb_A[e].T
+        assert np.max(np.abs(y)) <= 1 + 1e-12
+
+
+@pytest.mark.parametrize("name", ["circle2d", "helix3d", "segment3d"])
+def test_line_frame_is_rodrigues(name):
+    """The OBB matrix is diag(1/hw) R with R the rotation taking the unit
+    tangent at r = 0 to the x axis: its rows are orthogonal, row 0 is
+    parallel to the tangent, and R t / |t| = e1 (sign included)."""
+    coords, d, N = LINES[name]()
+    m = oracle.OracleMesh(coords, d, 1, N)
+    elem = np.arange(m.NE, dtype=np.int32)
+    _, J = m.forward_map(elem, np.zeros((m.NE, 1)), jacobian=True)
+    for e in range(m.NE):
+        A = m.obb_A[e]
+        Rn = A / np.linalg.norm(A, axis=1, keepdims=True)
+        np.testing.assert_allclose(Rn @ Rn.T, np.eye(d), atol=1e-12)
+        t = J[e, :, 0] / np.linalg.norm(J[e, :, 0])
+        np.testing.assert_allclose(Rn @ t, np.eye(d)[0], atol=1e-12)
+        assert np.linalg.det(Rn) > 0
+
+
+def test_line_projection_affine_closed_form():
+    """Straight line elements: the closest point of x* is the clamped
+    orthogonal projection on the element's chord, r* = clamp(2 t - 1) with
+    t = (x* - x_a).(x_b - x_a) / |x_b - x_a|^2, and dist2 its squared
+    distance (Sec. 3.2.1 constrained Newton, Sec. 4.4 codes)."""
+    xa, xb = np.array([0.1, -0.2, 0.3]), np.array([0.9, 0.5, -0.4])
+    coords = W.segment_lines(1, 3, xa, xb)
+    m = oracle.OracleMesh(coords, 3, 1, 4, tol=1.0)
+    rng = np.random.default_rng(30)
+    u = xb - xa
+    perp = np.cross(u, [0.3, 0.7, 0.1])
+    perp /= np.linalg.norm(perp)
+    t = rng.uniform(-0.3, 1.3, 300)
+    off = rng.uniform(-0.2, 0.2, 300) * np.linalg.norm(u) * 0.05
+    pts = xa + t[:, None] * u + off[:, None] * perp
+    code, elem, r, dist2 = m.findpts(pts)
+    tt = np.clip(((pts - xa) @ u) / (u @ u), 0, 1)
+    q = xa + tt[:, None] * u
+    found = code != 2
+    assert found.sum() > 100
+    np.testing.assert_allclose(r[found, 0], 2 * tt[found] - 1, atol=1e-12)
+    np.testing.assert_allclose(dist2[found], np.sum((pts - q) ** 2, axis=1)[found], rtol=1e-10, atol=1e-28)
+    assert np.all(code[found & (np.abs(off) * np.linalg.norm(u) > 1e-4)] == 1)
+
+
+@pytest.mark.parametrize("name", ["circle2d", "star2d", "helix3d"])
+def test_line_closest_point_brute_force(name):
+    """Points near a curved line mesh: the oracle's dist2 equals the minimum
+    over dense samples of the candidate elements' curves (those whose AABB
+    and OBB contain the point; to the sampling resolution, never above it by
+    more than rounding), and at an interior r* the residual is orthogonal to
+    the tangent (the KKT condition)."""
+    coords, d, N = LINES[name]()
+    m = oracle.OracleMesh(coords, d, 1, N, tol=1.0)
+    rng = np.random.default_rng(31)
+    el = rng.integers(0, m.NE, 300).astype(np.int32)
+    rt = rng.uniform(-1, 1, (300, 1))
+    x, J = m.forward_map(el, rt, jacobian=True)
+    pts = x + 0.003 * rng.standard_normal(x.shape)
+    code, elem, r, dist2 = m.findpts(pts)
+    rs = np.linspace(-1, 1, 4001)
+    curves = np.stack([m.forward_map(np.full(rs.size, e, np.int32), rs[:, None]) for e in range(m.NE)])
+    checked = 0
+    for p in np.flatnonzero(code == 1):
+        in_aabb = np.all((pts[p] >= m.aabb[:, :d]) & (pts[p] <= m.aabb[:, d:]), axis=1)
+        in_obb = np.max(np.abs(np.einsum("eij,ej->ei", m.obb_A, pts[p] - m.obb_c)), axis=1) <= 1
+        cand = np.flatnonzero(in_aabb & in_obb)  # the method's candidates (Sec. 3.2)
+        best = min(np.min(np.sum((curves[e] - pts[p]) ** 2, axis=1)) for e in cand)
+        assert dist2[p] <= best * (1 + 1e-9) + 1e-24
+        # the samples miss the true minimum by at most delta = half the sample spacing
+        delta = 0.5 * max(np.max(np.linalg.norm(np.diff(curves[e], axis=0), axis=1)) for e in cand)
+        assert dist2[p] >= best - 2 * np.sqrt(best) * delta - delta ** 2
+        if abs(r[p, 0]) < 1 - 1e-9:
+            xr, Jr = m.forward_map(elem[p:p + 1], r[p:p + 1], jacobian=True)
+            assert abs((pts[p] - xr[0]) @ Jr[0, :, 0]) <= 1e-9 * np.linalg.norm(Jr[0, :, 0]) * np.sqrt(dist2[p]) + 1e-14
+        checked += 1
+    assert checked > 100
+
+
+@pytest.mark.parametrize("name", ["circle2d", "helix3d"])
+def test_line_forward_map_recovered(name):
+    """Points x_e(r) on the curve are INTERIOR in element e with r recovered
+    to 1e-12 (Sec. 4.4: dist2 below eps_d)."""
+    coords, d, N = LINES[name]()
+    m = oracle.OracleMesh(coords, d, 1, N)
+    rng = np.random.default_rng(32)
+    el = rng.integers(0, m.NE, 500).astype(np.int32)
+    rt = rng.uniform(-0.98, 0.98, (500, 1))
+    code, elem, r, dist2 = m.findpts(m.forward_map(el, rt))
+    assert np.all(code == 0)
+    np.testing.assert_array_equal(elem, el)
+    np.testing.assert_allclose(r, rt, atol=1e-12)
