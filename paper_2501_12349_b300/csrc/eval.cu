@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(kEvalThreads)
     k_eval_f64(const BasisTab B, const int* __restrict__ code, const int* __restrict__ elem,
                const double* __restrict__ r, int64_t n, const double* __restrict__ field, int nc,
                int64_t NE, double* __restrict__ out, int* status) {
-  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  constexpr int NN = ipow(N, DR);
   const int64_t cs = NE * NN;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {

@@ -155,7 +155,7 @@ __device__ __forceinline__ void rel_point(const DevMesh& m, int64_t e, const dou
 // |d32 - d| <= 2 sqrt(D d) E + D E^2 + 8u d.
 template <int N, int D, int DR>
 __device__ int closest_node(const DevMesh& m, int e, const double (&xs)[D], const float (&xr)[D]) {
-  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  constexpr int NN = ipow(N, DR);
   const float* X32 = m.coords32 + (int64_t)e * NN;
   float b1 = INFINITY, b2 = INFINITY;
   int nb = 0;
@@ -301,136 +301,16 @@ __device__ __forceinline__ void eval_xG(const T* __restrict__ X, int64_t cs, con
     }
     map_eval_rolled<N, D, WANT_G, T>(X, cs, ph, dph, pt, dpt, x, G);
   } else {
-    T ph2[2][N], dph2[2][N];
+    T ph2[DR][N], dph2[DR][N];
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < DR; ++j)
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         ph2[j][i] = ph[j][i];
         dph2[j][i] = dph[j][i];
       }
-    map_eval<N, 2, D, WANT_G, T>(X, cs, ph2, dph2, x, G);
+    map_eval<N, DR, D, WANT_G, T>(X, cs, ph2, dph2, x, G);
   }
-}
-
-// HS_jk = sum_c dx_c d2x_c/dr_j dr_k at r (the beta term of Eq. newton_hessian).
-template <int N, int D, int DR, typename T>
-__device__ void hess_term(const T* __restrict__ X, int64_t cs, const BasisTab& B, const T (&r)[DR],
-                          const T (&dx)[D], const TSlots<N, T>& ts, T (&HS)[DR][DR]) {
-  T S[D * DR * DR];
-  if constexpr (DR == 3) {
-    T ph[3][N], dph[3][N], d2ph[3][N];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) lagrange2<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), r[j], ph[j], dph[j], d2ph[j]);
-    const Slots<T> pt = ts.slot(0), dpt = ts.slot(1), d2pt = ts.slot(2);
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      pt(k) = ph[2][k];
-      dpt(k) = dph[2][k];
-      d2pt(k) = d2ph[2][k];
-    }
-    map_hess_rolled<N, D, T>(X, cs, ph, dph, d2ph, pt, dpt, d2pt, S);
-  } else {
-    T ph[DR][N], dph[DR][N], d2ph[DR][N];
-#pragma unroll
-    for (int j = 0; j < DR; ++j) lagrange2<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), r[j], ph[j], dph[j], d2ph[j]);
-    map_hess<N, DR, D, T>(X, cs, ph, dph, d2ph, S);
-  }
-#pragma unroll
-  for (int j = 0; j < DR; ++j)
-#pragma unroll
-    for (int k = 0; k < DR; ++k) {
-      T s = T(0);
-#pragma unroll
-      for (int c = 0; c < D; ++c) s += dx[c] * S[(c * DR + j) * DR + k];
-      HS[j][k] = s;
-    }
-}
-
-// The beta term on the free block only, when every coordinate on the
-// boundary is held (the usual case on a face or edge): there phi(+-1) is a
-// unit vector, so the second derivatives along the free directions contract
-// only the face (2 free) or edge (1 free) slice of the element data.
-// Returns false when a boundary coordinate is free; the caller then
-// contracts the full element (hess_term).
-template <int N, int D, int DR, typename T>
-__device__ bool hess_term_slice(const T* __restrict__ X, int64_t cs, const BasisTab& B, const T (&r)[DR],
-                                const T (&dx)[D], const T (&G)[D * DR], T (&HS)[DR][DR]) {
-  int fr[DR], nf = 0, base = 0;
-  const int stride[3] = {1, N, N * N};
-#pragma unroll
-  for (int j = 0; j < DR; ++j) {
-    T g = T(0);
-#pragma unroll
-    for (int c = 0; c < D; ++c) g -= G[c * DR + j] * dx[c];
-    const bool onb = (r[j] == T(-1) || r[j] == T(1));
-    const bool held = (r[j] == T(-1) && g > T(0)) || (r[j] == T(1) && g < T(0));
-    if (onb && !held) return false;
-    if (held) base += (r[j] == T(1) ? N - 1 : 0) * stride[j];
-    else fr[nf++] = j;
-  }
-#pragma unroll
-  for (int j = 0; j < DR; ++j)
-#pragma unroll
-    for (int k = 0; k < DR; ++k) HS[j][k] = T(0);
-  if (nf == 0) return true;
-  const T* z = TabOf<T>::z(B);
-  const T* w = TabOf<T>::w(B);
-  auto rsel = [&](int j) {
-    T v = r[0];
-#pragma unroll
-    for (int q = 1; q < DR; ++q)
-      if (q == j) v = r[q];
-    return v;
-  };
-  if (nf == 1) {
-    const int a = fr[0], sa = stride[a];
-    T ph[N], dph[N], d2[N];
-    lagrange2<N, T>(z, w, rsel(a), ph, dph, d2);
-    T h = T(0);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const T* xe = X + c * cs + base;
-      T s = T(0);
-#pragma unroll
-      for (int i = 0; i < N; ++i) s = fma(ldg(xe + i * sa), d2[i], s);
-      h = fma(dx[c], s, h);
-    }
-    HS[a][a] = h;
-    return true;
-  }
-  const int a = fr[0], b = fr[1], sa = stride[a], sb = stride[b];
-  T pa[N], dpa[N], d2a[N], pb[N], dpb[N], d2b[N];
-  lagrange2<N, T>(z, w, rsel(a), pa, dpa, d2a);
-  lagrange2<N, T>(z, w, rsel(b), pb, dpb, d2b);
-  T haa = T(0), hab = T(0), hbb = T(0);
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const T* xe = X + c * cs + base;
-    T saa = T(0), sab = T(0), sbb = T(0);
-#pragma unroll
-    for (int ib = 0; ib < N; ++ib) {
-      T v0 = T(0), v1 = T(0), v2 = T(0);
-#pragma unroll
-      for (int ia = 0; ia < N; ++ia) {
-        const T v = ldg(xe + ia * sa + ib * sb);
-        v0 = fma(v, pa[ia], v0);
-        v1 = fma(v, dpa[ia], v1);
-        v2 = fma(v, d2a[ia], v2);
-      }
-      saa = fma(v2, pb[ib], saa);
-      sab = fma(v1, dpb[ib], sab);
-      sbb = fma(v0, d2b[ib], sbb);
-    }
-    haa = fma(dx[c], saa, haa);
-    hab = fma(dx[c], sab, hab);
-    hbb = fma(dx[c], sbb, hbb);
-  }
-  HS[a][a] = haa;
-  HS[a][b] = hab;
-  HS[b][a] = hab;
-  HS[b][b] = hbb;
-  return true;
 }
 
 // Gradient g = -G^T dx, held set, Hessian G^T G - beta HS, masked solve with

@@ -27,7 +27,7 @@ enum : int { E_INIT = 1, E_TRIAL = 2, E_RESTORE = 3 };
 // meshes of one launch share N, D, DR and so the basis table B.
 template <int N, int D, int DR, class Work>
 __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, unsigned long long* stats) {
-  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  constexpr int NN = ipow(N, DR);
   __shared__ double s_slab[DR == 3 ? 2 * N * kFindThreads : 1];
   __shared__ double s_hs[beta_entries<DR>() * kFindThreads];
   __shared__ double s_bscr[(kFindThreads / 32) * kBetaScratch];

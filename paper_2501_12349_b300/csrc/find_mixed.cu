@@ -9,8 +9,10 @@
 //     (values O(h), so the FP32 Jacobian keeps ~1e-7 relative accuracy).
 //  3. A candidate whose FP32 iteration converged strictly inside the element
 //     is parked for FP64 refinement: x(r) in FP64, the Gauss-Newton step
-//     solved in FP64 with the FP32 Jacobian, repeated until the step is below
-//     the Newton tolerance (typically two FP64 evaluations).  Parked lanes
+//     solved in FP64 with the FP32 Jacobian (volumes) or the FP64 one
+//     (surfaces and lines, whose converged residual is not zero), repeated
+//     until the step is below the Newton tolerance (typically two FP64
+//     evaluations).  Parked lanes
 //     wait until most of their warp is parked, so the FP64 work runs with
 //     nearly full warps.
 //  4. A candidate the FP32 iteration leaves clearly outside (on the boundary
@@ -44,7 +46,7 @@ inline unsigned long long* fallback_stats(unsigned long long* stats) { return st
 template <int N, int D, int DR, class Work>
 __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B, int* __restrict__ queue,
                                                 int* __restrict__ qcount, unsigned long long* stats) {
-  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  constexpr int NN = ipow(N, DR);
   __shared__ double s_slab64[DR == 3 ? 2 * N * kFindThreads : 1];
   __shared__ float s_slab32[DR == 3 ? 2 * N * kFindThreads : 1];
   __shared__ float s_hs[beta_entries<DR>() * kFindThreads];
@@ -204,12 +206,20 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
     // ---- FP64 refinement, warp-batched --------------------------------------
     if ((__popc(parked) >= kPark || busy == 0) && mode == X_PARK) {
       ++cnt.v[4];
+      // Volumes converge to dx = 0, where the FP32 Jacobian only sets the
+      // rate.  On a surface or line the converged residual is normal to the
+      // manifold and not zero, and the stationary point G^T dx = 0 moves by
+      // |dx| times the Jacobian's error, so there G is evaluated in FP64.
+      constexpr bool kG64 = DR < D;
       double xv[D], dxd[D], Gd[D * DR];
-      eval_xG<N, D, DR, false, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r64, ts64, xv, nullptr);
+      eval_xG<N, D, DR, kG64, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r64, ts64, xv,
+                                      kG64 ? Gd : nullptr);
 #pragma unroll
       for (int c = 0; c < D; ++c) dxd[c] = xs[c] - xv[c];
+      if constexpr (!kG64) {
 #pragma unroll
-      for (int q2 = 0; q2 < D * DR; ++q2) Gd[q2] = (double)G[q2];
+        for (int q2 = 0; q2 < D * DR; ++q2) Gd[q2] = (double)G[q2];
+      }
       // Gauss-Newton step in FP64: (G^T G) s = G^T dx
       double H[DR][DR], b[DR], s[DR];
 #pragma unroll
@@ -229,10 +239,16 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
       double dprod = 1.0;
 #pragma unroll
       for (int j = 0; j < DR; ++j) dprod *= H[j][j];
-      double det = (DR == 2) ? H[0][0] * H[1][1] - H[0][1] * H[1][0]
-                             : H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
-                                   H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
-                                   H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+      double det;
+      if constexpr (DR == 1) {
+        det = H[0][0];
+      } else if constexpr (DR == 2) {
+        det = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+      } else {
+        det = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
+              H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+              H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+      }
       bool ok = spd_solve<DR, double>(H, b, s) && det > 1e-8 * dprod;
       bool inside = ok;
       double mx = 0.0, rnn[DR];

@@ -114,7 +114,7 @@ __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, co
           g2 = fma(ak, dph[2][k], g2);
         }
       }
-    } else {
+    } else if constexpr (DR == 2) {
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         T a = T(0), b = T(0);
@@ -130,75 +130,19 @@ __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, co
           g1 = fma(a, dph[1][j], g1);
         }
       }
+    } else {  // line elements
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const T v = ldg(xe + i);
+        xv = fma(v, ph[0][i], xv);
+        if (WANT_G) g0 = fma(v, dph[0][i], g0);
+      }
     }
     x[c] = xv;
     if (WANT_G) {
       G[c * DR + 0] = g0;
-      G[c * DR + 1] = g1;
+      if constexpr (DR >= 2) G[c * DR + 1] = g1;
       if constexpr (DR == 3) G[c * DR + 2] = g2;
-    }
-  }
-}
-
-// Second derivatives S[(c*DR + j)*DR + k] = d^2 x_c / dr_j dr_k (symmetric).
-template <int N, int DR, int D, typename T>
-__device__ __forceinline__ void map_hess(const T* __restrict__ X, int64_t cs, const T (&ph)[DR][N],
-                                         const T (&dph)[DR][N], const T (&d2ph)[DR][N], T* S) {
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const T* xe = X + c * cs;
-    if constexpr (DR == 3) {
-      T rr = 0, rs = 0, rt = 0, ss = 0, st = 0, tt = 0;
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        T p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0, p6 = 0;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          T a = 0, b = 0, c2 = 0;
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const T v = ldg(xe + (k * N + j) * N + i);
-            a = fma(v, ph[0][i], a);
-            b = fma(v, dph[0][i], b);
-            c2 = fma(v, d2ph[0][i], c2);
-          }
-          p1 = fma(c2, ph[1][j], p1);
-          p2 = fma(b, dph[1][j], p2);
-          p3 = fma(b, ph[1][j], p3);
-          p4 = fma(a, d2ph[1][j], p4);
-          p5 = fma(a, dph[1][j], p5);
-          p6 = fma(a, ph[1][j], p6);
-        }
-        rr = fma(p1, ph[2][k], rr);
-        rs = fma(p2, ph[2][k], rs);
-        rt = fma(p3, dph[2][k], rt);
-        ss = fma(p4, ph[2][k], ss);
-        st = fma(p5, dph[2][k], st);
-        tt = fma(p6, d2ph[2][k], tt);
-      }
-      T* Sc = S + c * 9;
-      Sc[0] = rr; Sc[1] = rs; Sc[2] = rt;
-      Sc[3] = rs; Sc[4] = ss; Sc[5] = st;
-      Sc[6] = rt; Sc[7] = st; Sc[8] = tt;
-    } else {
-      T rr = 0, rs = 0, ss = 0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        T a = 0, b = 0, c2 = 0;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const T v = ldg(xe + j * N + i);
-          a = fma(v, ph[0][i], a);
-          b = fma(v, dph[0][i], b);
-          c2 = fma(v, d2ph[0][i], c2);
-        }
-        rr = fma(c2, ph[1][j], rr);
-        rs = fma(b, dph[1][j], rs);
-        ss = fma(a, d2ph[1][j], ss);
-      }
-      T* Sc = S + c * 4;
-      Sc[0] = rr; Sc[1] = rs;
-      Sc[2] = rs; Sc[3] = ss;
     }
   }
 }
@@ -259,58 +203,16 @@ __device__ __forceinline__ void map_eval_rolled(const T* __restrict__ X, int64_t
   }
 }
 
-// map_hess for hexes with the t-loop rolled (t-basis values and their first
-// and second derivatives in slots pt, dpt, d2pt).
-template <int N, int D, typename T>
-__device__ __forceinline__ void map_hess_rolled(const T* __restrict__ X, int64_t cs,
-                                                const T (&ph)[3][N], const T (&dph)[3][N],
-                                                const T (&d2ph)[3][N], const Slots<T>& pt,
-                                                const Slots<T>& dpt, const Slots<T>& d2pt, T* S) {
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const T* xe = X + c * cs;
-    T rr = 0, rs = 0, rt = 0, ss = 0, st = 0, tt = 0;
-#pragma unroll 1
-    for (int k = 0; k < N; ++k) {
-      T p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0, p6 = 0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        T a = 0, b = 0, c2 = 0;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const T v = ldg(xe + (k * N + j) * N + i);
-          a = fma(v, ph[0][i], a);
-          b = fma(v, dph[0][i], b);
-          c2 = fma(v, d2ph[0][i], c2);
-        }
-        p1 = fma(c2, ph[1][j], p1);
-        p2 = fma(b, dph[1][j], p2);
-        p3 = fma(b, ph[1][j], p3);
-        p4 = fma(a, d2ph[1][j], p4);
-        p5 = fma(a, dph[1][j], p5);
-        p6 = fma(a, ph[1][j], p6);
-      }
-      const T tk = pt(k), dtk = dpt(k), d2tk = d2pt(k);
-      rr = fma(p1, tk, rr);
-      rs = fma(p2, tk, rs);
-      rt = fma(p3, dtk, rt);
-      ss = fma(p4, tk, ss);
-      st = fma(p5, dtk, st);
-      tt = fma(p6, d2tk, tt);
-    }
-    T* Sc = S + c * 9;
-    Sc[0] = rr; Sc[1] = rs; Sc[2] = rt;
-    Sc[3] = rs; Sc[4] = ss; Sc[5] = st;
-    Sc[6] = rt; Sc[7] = st; Sc[8] = tt;
-  }
-}
-
 // Solves A s = b for a symmetric DR x DR matrix by cofactors when A is
 // positive definite (all leading principal minors > 0, the same sign test as
 // the pivots of a Cholesky factorisation); returns false otherwise.
 template <int DR, typename T>
 __device__ __forceinline__ bool spd_solve(const T (&A)[DR][DR], const T (&b)[DR], T (&s)[DR]) {
-  if constexpr (DR == 2) {
+  if constexpr (DR == 1) {
+    if (!(A[0][0] > T(0))) return false;
+    s[0] = b[0] / A[0][0];
+    return true;
+  } else if constexpr (DR == 2) {
     const T det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
     if (!(A[0][0] > T(0)) || !(det > T(0))) return false;
     const T inv = T(1) / det;

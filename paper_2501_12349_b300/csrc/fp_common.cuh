@@ -153,8 +153,12 @@ namespace fp {
 template <int V>
 using ic = std::integral_constant<int, V>;
 
+// N^dr: nodes of a line, quad or hex element.
+__host__ __device__ constexpr int ipow(int n, int k) { return k == 0 ? 1 : n * ipow(n, k - 1); }
+
 // Calls f(ic<N>, ic<D>, ic<DR>) for the element shapes the library is built
-// for: N in 2..FP_MAX_N and (d, dr) in {(2,2), (3,3), (3,2)}.
+// for: N in 2..FP_MAX_N and (d, dr) in {(2,2), (3,3), (3,2), (2,1), (3,1)}:
+// quads, hexes, surface quads and line elements in 2D and 3D.
 template <typename F>
 int dispatch_shape(int N, int d, int dr, F&& f) {
   auto withN = [&](auto Dc, auto DRc) -> int {
@@ -172,6 +176,8 @@ int dispatch_shape(int N, int d, int dr, F&& f) {
   if (d == 2 && dr == 2) return withN(ic<2>{}, ic<2>{});
   if (d == 3 && dr == 3) return withN(ic<3>{}, ic<3>{});
   if (d == 3 && dr == 2) return withN(ic<3>{}, ic<2>{});
+  if (d == 2 && dr == 1) return withN(ic<2>{}, ic<1>{});
+  if (d == 3 && dr == 1) return withN(ic<3>{}, ic<1>{});
   return FP_EINVAL;
 }
 

@@ -50,7 +50,7 @@ using Clock = std::chrono::steady_clock;
 template <int N, int DR>
 __global__ void __launch_bounds__(128)
     k_serve_eval(const BatchItem* __restrict__ items, int nitems, int64_t total, const BasisTab B) {
-  constexpr int NN = (DR == 3) ? N * N * N : N * N;
+  constexpr int NN = ipow(N, DR);
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     int lo = 0, hi = nitems - 1;

@@ -219,27 +219,67 @@ __device__ void expand(int d, const double* lo, const double* hi, double tol, do
   }
 }
 
+// The rotation R taking the unit tangent u = t/|t| of a line element to the
+// x axis (Sec. 4.2, Rodrigues' formula): in 2D the plane rotation with rows
+// (u0, u1), (-u1, u0); in 3D R = I + sin K + (1 - cos) K^2 with K the
+// cross-product matrix of the unit axis u x e1 and cos = u0 (a tangent
+// along -e1 turns by pi about e3).  Row-major, D x D.
+template <int D>
+__device__ void line_rotation(const double* t, double* R) {
+  double nt = 0.0;
+  for (int c = 0; c < D; ++c) nt += t[c] * t[c];
+  nt = sqrt(nt);
+  double u[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < D; ++c) u[c] = t[c] / nt;
+  if (D == 2) {
+    R[0] = u[0];
+    R[1] = u[1];
+    R[2] = -u[1];
+    R[3] = u[0];
+    return;
+  }
+  const double ax1 = u[2], ax2 = -u[1];  // u x e1 = (0, u2, -u1)
+  const double sn = sqrt(ax1 * ax1 + ax2 * ax2), cs = u[0];
+  for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  if (sn == 0.0) {
+    R[0] = cs > 0.0 ? 1.0 : -1.0;
+    R[4] = cs > 0.0 ? 1.0 : -1.0;
+    return;
+  }
+  const double k[3] = {0.0, ax1 / sn, ax2 / sn};
+  const double K[9] = {0.0, -k[2], k[1], k[2], 0.0, -k[0], -k[1], k[0], 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double k2 = 0.0;
+      for (int m = 0; m < 3; ++m) k2 += K[i * 3 + m] * K[m * 3 + j];
+      R[i * 3 + j] += sn * K[i * 3 + j] + (1.0 - cs) * k2;
+    }
+}
+
 // One CTA per element.  AABB: bounds of each coordinate over the element's
 // boundary pieces (quad edges, hex faces) or over the element itself
-// (surface quads), Eqs. 1D_bound_final / 2D_function_bound.  OBB: the same
-// bounds of the nodes mapped by T = J_c^{-1} (volumes, Eq.
-// OBB_transformation) or T = [t1 t2 n]^{-1} (surfaces; this is the paper's
-// R2 R1 of Sec. 4.2 written as one inverse: R1 is a rotation taking n to
-// e3, and R2 R1 maps t1, t2, n to e1, e2, e3).
+// (surface quads, lines), Eqs. 1D_bound_final / 2D_function_bound.  OBB: the
+// same bounds of the nodes mapped by T = J_c^{-1} (volumes, Eq.
+// OBB_transformation), T = [t1 t2 n]^{-1} (surface quads; this is the
+// paper's R2 R1 of Sec. 4.2 written as one inverse: R1 is a rotation taking
+// n to e3, and R2 R1 maps t1, t2, n to e1, e2, e3) or the Rodrigues
+// rotation of line_rotation (lines).
 template <int N, int D, int DR>
 __global__ void __launch_bounds__(kBoxThreads)
     k_boxes(const double* __restrict__ coords, int64_t NE, const double* __restrict__ tab, int M,
             BasisTab B, double tol, double* __restrict__ aabb, double* __restrict__ obb_c,
             double* __restrict__ obb_A, double* __restrict__ linmap, int* status) {
-  constexpr int NN = (DR == 3) ? N * N * N : N * N;
-  constexpr int NPIECE = (DR == 3) ? 6 : (D == 2 ? 4 : 1);
-  constexpr int PIECE = (DR == 3 || D == 3) ? N * N : N;  // values per piece
+  constexpr int NN = ipow(N, DR);
+  // bounding pieces: the 6 faces of a hex, the 4 edges of a quad, the
+  // element itself for a surface quad or a line
+  constexpr int NPIECE = (DR == 3) ? 6 : ((D == 2 && DR == 2) ? 4 : 1);
+  constexpr int PIECE = (DR == 3 || (D == 3 && DR == 2)) ? N * N : N;  // values per piece
   const TabLayout L(N, M);
   __shared__ double X[D * NN];
   __shared__ double Xt[D * NN];
   __shared__ double u[N * N];
   __shared__ double lin[3];
-  __shared__ double T[9], Ti[9], xc[3];
+  __shared__ double T[9], Ti[9], xc[3], tlin[3];
   __shared__ double red[2][kBoxThreads / 32];
   __shared__ double blo[2][3], bhi[2][3];
   const int tid = threadIdx.x;
@@ -264,10 +304,13 @@ __global__ void __launch_bounds__(kBoxThreads)
           g[0] += v * dph[i] * ph[j] * ph[k];
           g[1] += v * ph[i] * dph[j] * ph[k];
           g[2] += v * ph[i] * ph[j] * dph[k];
-        } else {
+        } else if (DR == 2) {
           xv += v * ph[i] * ph[j];
           g[0] += v * dph[i] * ph[j];
           g[1] += v * ph[i] * dph[j];
+        } else {
+          xv += v * ph[i];
+          g[0] += v * dph[i];
         }
       }
       xc[c] = xv;
@@ -276,6 +319,15 @@ __global__ void __launch_bounds__(kBoxThreads)
     double Mx[9];
     if (DR == D) {
       for (int q = 0; q < D * D; ++q) Mx[q] = J[q];
+    } else if (DR == 1) {
+      // lines (Sec. 4.2): R = the Rodrigues rotation taking t/|t| to e1;
+      // Mx = R^T, so that T = Mx^{-1} = R
+      double R[9], tt = 0.0;
+      line_rotation<D>(J, R);
+      for (int q = 0; q < D; ++q) tt += J[q] * J[q];
+      for (int q = 0; q < D; ++q) tlin[q] = J[q] / tt;
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) Mx[a * D + b] = R[b * D + a];
     } else {  // [t1 t2 n/|n|] as columns
       const double t1[3] = {J[0], J[2], J[4]}, t2[3] = {J[1], J[3], J[5]};
       double n[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
@@ -336,7 +388,7 @@ __global__ void __launch_bounds__(kBoxThreads)
             const int j = fixed == 0 ? a : (fixed == 1 ? val : b);
             const int k = fixed == 2 ? val : b;
             n = i + N * (j + N * k);
-          } else if (D == 3) {
+          } else if (D == 3 || DR == 1) {
             n = idx;
           } else {
             const int a = idx;
@@ -439,6 +491,8 @@ __global__ void __launch_bounds__(kBoxThreads)
       linmap[e * 12 + c] = xc[c];
       for (int q = 0; q < D; ++q) linmap[e * 12 + 3 + c * 3 + q] = T[c * D + q];
     }
+    if (DR == 1)  // the linear start of a line: r = t.(x - x_c) / |t|^2
+      for (int q = 0; q < D; ++q) linmap[e * 12 + 3 + q] = tlin[q];
     expand(D, blo[1], bhi[1], tol, mid, hw);
     for (int c = 0; c < D; ++c) {
       double s = xc[c];
@@ -763,7 +817,8 @@ extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int6
   if (!out) return FP_EINVAL;
   *out = nullptr;
   if (!coords_dev || NE <= 0 || NE > INT32_MAX) return FP_EINVAL;
-  if (!((d == 2 && dr == 2) || (d == 3 && dr == 3) || (d == 3 && dr == 2))) return FP_EINVAL;
+  if (!((d == 2 && dr == 2) || (d == 3 && dr == 3) || (d == 3 && dr == 2) || (dr == 1 && (d == 2 || d == 3))))
+    return FP_EINVAL;
   const int N = order + 1;
   if (order < 1) return FP_EINVAL;
   if (N > FP_MAX_N) return FP_EUNSUPPORTED;
@@ -781,7 +836,7 @@ extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int6
   m->d = d;
   m->dr = dr;
   m->N = N;
-  m->ne = (dr == 3) ? N * N * N : N * N;
+  m->ne = ipow(N, dr);
   m->M = o.M;
   m->NE = NE;
   m->opts = o;

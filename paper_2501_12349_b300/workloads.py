@@ -170,19 +170,25 @@ def star_lines(n: int, order: int, a: float = 0.15, k: int = 5) -> np.ndarray:
 
 
 def projection_points(coords: np.ndarray, rng: np.random.Generator, tangential: float = 0.3,
-                      normal: float = 0.01) -> np.ndarray:
+                      normal: float = 0.5) -> np.ndarray:
     """Closest-point projection workload (the tangential relaxation of the
     paper's r-adaptivity example): every node of a 2D line mesh moved along
-    the curve's tangent by up to +-tangential h and off it by up to
-    +-normal h (h = the element's chord), as a mesh optimiser would move
-    boundary nodes.  Returns points [NE*N][2]."""
+    the curve's tangent by up to +-tangential h (h = the element's chord)
+    and off it by up to +-normal s (s = the element's sagitta, the largest
+    distance of its nodes from the chord), as a mesh optimiser moves
+    boundary nodes, its steps scaled down so the nodes stay inside the
+    (100%-expanded) boxes.  Returns points [NE*N][2]."""
     d, NE, N = coords.shape
-    h = np.linalg.norm(coords[:, :, -1] - coords[:, :, 0], axis=0)  # [NE]
+    chord = coords[:, :, -1] - coords[:, :, 0]
+    h = np.linalg.norm(chord, axis=0)  # [NE]
+    ch = chord / h
+    rel = coords - coords[:, :, :1]
+    sag = np.max(np.abs(rel[0] * ch[1][:, None] - rel[1] * ch[0][:, None]), axis=1)  # [NE]
     tan = np.gradient(coords, axis=2)
     tan = tan / np.linalg.norm(tan, axis=0, keepdims=True)
     nrm = np.stack([-tan[1], tan[0]])
     st = rng.uniform(-tangential, tangential, (NE, N)) * h[:, None]
-    sn = rng.uniform(-normal, normal, (NE, N)) * h[:, None]
+    sn = rng.uniform(-normal, normal, (NE, N)) * sag[:, None]
     x = coords + st[None] * tan + sn[None] * nrm
     return np.ascontiguousarray(x.reshape(d, -1).T)
 
