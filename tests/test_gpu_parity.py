@@ -310,3 +310,31 @@ def test_many_fields_one_find(fp, torch):
     compare_eval(np.concatenate(fields), om.NE, (order + 1) ** 3, o[1], om.eval(np.concatenate(fields), *o[:3]),
                  uo, "many fields")
     m.close()
+
+
+def test_distributed_find_single_rank_nccl(fp, torch):
+    """The multi-rank Find (Psi_G, Sec. 3.1.4; Sec. 3.2) on CUDA tensors over
+    NCCL with one rank, the library's find as the local search: identical to
+    the plain find (the routing moves nothing, and the device path of every
+    exchange and of the merge runs)."""
+    import socket
+    import torch.distributed as dist
+    from paper_2501_12349_b300 import distributed as Dm
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    dist.init_process_group("nccl", rank=0, world_size=1, init_method=f"tcp://127.0.0.1:{port}")
+    try:
+        coords, d, dr, order, h = CASES["hex3d_p4"]()
+        m = gpu_mesh(fp, torch, coords, d, dr, order)
+        aabb, _, _ = m.boxes()
+        gmap = Dm.GlobalMap.build(aabb, d)
+        pts = torch.from_numpy(np.random.default_rng(15).uniform(-0.1, 1.1, (20000, 3))).cuda()
+        code, rank, elem, r, d2 = Dm.find(m.find, pts, gmap)
+        ref = m.find(pts)
+        assert torch.equal(code, ref[0]) and torch.equal(elem, ref[1])
+        assert torch.equal(r, ref[2]) and torch.equal(d2, ref[3])
+        assert torch.all(rank[code != 2] == 0) and torch.all(rank[code == 2] == -1)
+        m.close()
+    finally:
+        dist.destroy_process_group()
