@@ -209,7 +209,10 @@ typedef struct {
 typedef struct fp_batch_s* fp_batch;
 
 /* Builds the plan (item tables on the device, a scratch queue per shape for
- * FP_MIXED) and captures the graph.  Launch shapes come from this process's
+ * FP_MIXED) and captures the graph.  A shape with at least 16384 points whose
+ * items' meshes all use FP_ORDER_CELL takes its points grouped by (item,
+ * Psi_L cell), as fp_findpts does (scratch: 8 bytes per point and per
+ * cell); the outputs are the same either way.  Launch shapes come from this process's
  * earlier fp_batch_autotune results for the same shape, precision and point
  * count (power-of-two bucket), else defaults.  Synchronous.
  * Errors: FP_EINVAL (bad index, NULL buffer, n > 2^31-1), FP_ENOMEM,

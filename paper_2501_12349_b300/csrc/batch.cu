@@ -21,9 +21,6 @@
 
 namespace fp {
 
-int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
-                       const BasisTab& B, int precision, int ctas_per_sm, int clog2, int* queue,
-                       int* qcount, unsigned long long* stats, cudaStream_t st);
 
 namespace {
 
@@ -52,9 +49,9 @@ __global__ void __launch_bounds__(kEvalThreads)
       for (int c = 0; c < it.nc; ++c) it.out[(int64_t)c * it.n + p] = 0.0;
       continue;
     }
-    double ph[DR][N], dph[DR][N];
+    double ph[DR][N], dph[DR][N] = {};  // dph unused: values only
 #pragma unroll
-    for (int j = 0; j < DR; ++j) lagrange<N, double>(B.z, B.w, it.r[p * DR + j], ph[j], dph[j]);
+    for (int j = 0; j < DR; ++j) lagrange_values<N, double>(B.z, B.w, it.r[p * DR + j], ph[j]);
     for (int c = 0; c < it.nc; ++c) {
       double v;
       map_eval<N, DR, 1, false, double>(it.field + (c * NE + e) * NN, 0, ph, dph, &v, nullptr);
@@ -97,6 +94,9 @@ struct ClassPlan {
   int64_t total = 0;
   BatchItem* d_items = nullptr;
   int* d_queue = nullptr;  // total + 1 ints: mixed-path queue and its counter
+  int* d_order = nullptr;  // cell-order scratch (NULL: points as given)
+  int64_t buckets = 0;     // sum over items of (Psi_L cells + 1)
+  bool unordered = false;  // some item's mesh takes its points as given
   bool has_field = false;
   Tuning tune;
   cudaStream_t side = nullptr;
@@ -125,8 +125,11 @@ int enqueue_class(ClassPlan& c, int precision, const Tuning& t, cudaStream_t st)
   if (c.total == 0) return FP_OK;
   int* qcount = c.d_queue + c.total;
   if (precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qcount, 0, sizeof(int), st));
+  int* order = nullptr;
+  if (c.d_order)
+    FP_TRY(batch_cell_order(c.d_items, (int)c.items.size(), c.total, c.d, c.buckets, c.d_order, &order, st));
   FP_TRY(launch_batch_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, precision,
-                            t.ctas_per_sm, t.clog2, c.d_queue, qcount, nullptr, st));
+                            t.ctas_per_sm, t.clog2, order, c.d_queue, qcount, nullptr, st));
   if (c.has_field) FP_TRY(launch_eval_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, st));
   return FP_OK;
 }
@@ -176,6 +179,7 @@ void free_plan(fp_batch_s* b) {
   for (auto& c : b->classes) {
     cudaFree(c.d_items);
     cudaFree(c.d_queue);
+    cudaFree(c.d_order);
     if (c.side) cudaStreamDestroy(c.side);
     if (c.join) cudaEventDestroy(c.join);
   }
@@ -237,8 +241,11 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
     bi.out = items[i].out;
     if (bi.field) c.has_field = true;
     if (bi.n > 0) {
+      bi.cell_base = c.buckets;
+      c.buckets += m->ncell + 1;
       c.items.push_back(bi);
       c.total += bi.n;
+      if (m->opts.point_order != FP_ORDER_CELL) c.unordered = true;
     }
   }
   int rc = FP_OK;
@@ -260,6 +267,12 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
     }
     if (cudaMalloc(&c.d_items, sizeof(BatchItem) * c.items.size()) != cudaSuccess ||
         cudaMalloc(&c.d_queue, sizeof(int) * (size_t)(c.total + 1)) != cudaSuccess) {
+      rc = FP_ENOMEM;
+      break;
+    }
+    // the cell order (as for single-mesh calls of at least 16384 points)
+    if (!c.unordered && c.total >= (1 << 14) && c.buckets + 1 < INT32_MAX &&
+        cudaMalloc(&c.d_order, sizeof(int) * (size_t)(2 * c.total + 2 * c.buckets + 1)) != cudaSuccess) {
       rc = FP_ENOMEM;
       break;
     }

@@ -30,9 +30,9 @@ __global__ void __launch_bounds__(kEvalThreads)
       for (int c = 0; c < nc; ++c) out[(int64_t)c * n + p] = 0.0;
       continue;
     }
-    double ph[DR][N], dph[DR][N];
+    double ph[DR][N], dph[DR][N] = {};  // dph unused: values only
 #pragma unroll
-    for (int j = 0; j < DR; ++j) lagrange<N, double>(B.z, B.w, __ldg(r + p * DR + j), ph[j], dph[j]);
+    for (int j = 0; j < DR; ++j) lagrange_values<N, double>(B.z, B.w, __ldg(r + p * DR + j), ph[j]);
     for (int c = 0; c < nc; ++c) {
       double v;
       map_eval<N, DR, 1, false, double>(field + c * cs + (int64_t)e * NN, 0, ph, dph, &v, nullptr);

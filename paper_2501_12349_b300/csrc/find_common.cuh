@@ -291,7 +291,15 @@ __device__ __forceinline__ void eval_xG(const T* __restrict__ X, int64_t cs, con
                                         const T (&re)[DR], const TSlots<N, T>& ts, T* x, T* G) {
   T ph[3][N], dph[3][N];
 #pragma unroll
-  for (int j = 0; j < DR; ++j) lagrange<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), re[j], ph[j], dph[j]);
+  for (int j = 0; j < DR; ++j) {
+    if constexpr (WANT_G) {
+      lagrange<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), re[j], ph[j], dph[j]);
+    } else {
+      lagrange_values<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), re[j], ph[j]);
+#pragma unroll
+      for (int i = 0; i < N; ++i) dph[j][i] = T(0);
+    }
+  }
   if constexpr (DR == 3) {
     const Slots<T> pt = ts.slot(0), dpt = ts.slot(1);
 #pragma unroll
@@ -472,6 +480,7 @@ struct BatchItem {
   const double* field;
   int nc;
   double* out;
+  int64_t cell_base;  // first bucket of this item's Psi_L cells in the batch's cell order
 };
 
 // A batch of items of one element shape; the point sequence is the items'
@@ -513,9 +522,19 @@ int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, 
 int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
                             int* elem, double* r, double* dist2, int* queue, int* qcount,
                             unsigned long long* stats, cudaStream_t st);
+// One element shape of a batch (find_mixed.cu): the find kernel(s) over
+// all items; order (may be NULL) is the batch cell order of the points.
+int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
+                       const BasisTab& B, int precision, int ctas_per_sm, int clog2, const int* order,
+                       int* queue, int* qcount, unsigned long long* stats, cudaStream_t st);
 // Cell-grouped point order (order.cu): scratch of cell_order_ints ints;
 // *perm points into it.
 int64_t cell_order_ints(const fp_mesh_s* m, int64_t n);
 int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, int** perm, cudaStream_t st);
+// The same for one element shape of a batch: the points of all items grouped
+// by (item, Psi_L cell); buckets = sum over items of (cells + 1), with each
+// item's cell_base set; scratch of 2 total + 2 buckets + 1 ints.
+int batch_cell_order(const BatchItem* items, int nitems, int64_t total, int d, int64_t buckets, int* scratch,
+                     int** perm, cudaStream_t st);
 
 }  // namespace fp

@@ -346,10 +346,10 @@ __global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
 
 template <int N, int D, int DR>
 __global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
-    k_find_mixed_batch(const BatchItem* __restrict__ items, int nitems, int64_t total, const BasisTab B,
-                       int* __restrict__ queue, int* __restrict__ qcount, int clog2,
-                       unsigned long long* stats) {
-  const BatchWork<D, DR> w{items, nitems, nullptr, total, clog2};
+    k_find_mixed_batch(const BatchItem* __restrict__ items, int nitems, int64_t total,
+                       const int* __restrict__ gidx, const BasisTab B, int* __restrict__ queue,
+                       int* __restrict__ qcount, int clog2, unsigned long long* stats) {
+  const BatchWork<D, DR> w{items, nitems, gidx, total, clog2};
   find_mixed_loop<N, D, DR>(w, B, queue, qcount, stats);
 }
 
@@ -382,19 +382,19 @@ namespace fp {
 // One element shape of a batch: the mixed kernel over all items, then the
 // FP64 kernel over the queued global indices (queue capacity >= total).
 int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
-                       const BasisTab& B, int precision, int ctas_per_sm, int clog2, int* queue,
-                       int* qcount, unsigned long long* stats, cudaStream_t st) {
+                       const BasisTab& B, int precision, int ctas_per_sm, int clog2, const int* order,
+                       int* queue, int* qcount, unsigned long long* stats, cudaStream_t st) {
   return dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int NN = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
     if (ctas_per_sm <= 0) ctas_per_sm = precision == FP_MIXED ? kMixedCtasPerSm : f64_ctas(NN);
     const int blocks = persistent_blocks(total, ctas_per_sm);
     if (precision == FP_MIXED) {
-      k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, B, queue, qcount,
-                                                                     clog2, stats);
+      k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, order, B, queue,
+                                                                     qcount, clog2, stats);
       k_find_f64_batch<NN, D, DR><<<persistent_blocks(total, f64_ctas(NN)), kFindThreads, 0, st>>>(
           items, nitems, total, queue, qcount, B, clog2, fallback_stats(stats));
     } else {
-      k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, nullptr, nullptr, B,
+      k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, order, nullptr, B,
                                                                    clog2, stats);
     }
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;

@@ -50,6 +50,23 @@ __device__ __forceinline__ void lagrange(const T* z, const T* w, T r, T* phi, T*
   }
 }
 
+// Values only: phi_i(r) = w_i (prefix product)_i (suffix product)_i.
+template <int N, typename T>
+__device__ __forceinline__ void lagrange_values(const T* z, const T* w, T r, T* phi) {
+  T d[N], p[N];
+#pragma unroll
+  for (int m = 0; m < N; ++m) d[m] = r - z[m];
+  p[0] = T(1);
+#pragma unroll
+  for (int i = 1; i < N; ++i) p[i] = p[i - 1] * d[i - 1];
+  T s = T(1);
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    phi[i] = w[i] * (p[i] * s);
+    s = s * d[i];
+  }
+}
+
 // Values, first and second derivatives.
 template <int N, typename T>
 __device__ __forceinline__ void lagrange2(const T* z, const T* w, T r, T* phi, T* dphi, T* d2phi) {

@@ -45,7 +45,54 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <int D>
+__global__ void __launch_bounds__(256)
+    k_batch_point_cells(const BatchItem* __restrict__ items, int nitems, int64_t total, int* __restrict__ key,
+                        int* __restrict__ counts) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {  // last item with start <= g
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].start <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchItem& it = items[lo];
+    const int64_t p = g - it.start;
+    double xs[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) xs[c] = __ldg(it.pts + p * D + c);
+    int64_t ncell = 1;
+#pragma unroll
+    for (int c = 0; c < D; ++c) ncell *= it.m.NL;
+    const int64_t cell = point_cell<D>(it.m, xs);
+    const int k = (int)(it.cell_base + (cell < 0 ? ncell : cell));
+    key[g] = k;
+    atomicAdd(counts + k, 1);
+  }
+}
+
 }  // namespace
+
+int batch_cell_order(const BatchItem* items, int nitems, int64_t total, int d, int64_t buckets, int* scratch,
+                     int** perm, cudaStream_t st) {
+  int* p = scratch;               // [total]
+  int* key = p + total;           // [total]
+  int* counts = key + total;      // [buckets]
+  int* start = counts + buckets;  // [buckets + 1]
+  FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)buckets, st));
+  const int blocks = (int)((total + 255) / 256 < 8 * 148 ? (total + 255) / 256 : 8 * 148);
+  if (d == 2)
+    k_batch_point_cells<2><<<blocks, 256, 0, st>>>(items, nitems, total, key, counts);
+  else
+    k_batch_point_cells<3><<<blocks, 256, 0, st>>>(items, nitems, total, key, counts);
+  k_scan<<<1, 1024, 0, st>>>(counts, buckets, start);
+  FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)buckets, st));
+  k_point_scatter<<<blocks, 256, 0, st>>>(key, total, start, counts, p);
+  FP_CUDA_TRY(cudaGetLastError());
+  *perm = p;
+  return FP_OK;
+}
 
 int64_t cell_order_ints(const fp_mesh_s* m, int64_t n) { return 2 * n + 2 * (m->ncell + 1) + 1; }
 

@@ -37,9 +37,6 @@
 
 namespace fp {
 
-int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
-                       const BasisTab& B, int precision, int ctas_per_sm, int clog2, int* queue,
-                       int* qcount, unsigned long long* stats, cudaStream_t st);
 
 namespace {
 
@@ -68,9 +65,9 @@ __global__ void __launch_bounds__(128)
       for (int c = 0; c < it.nc; ++c) it.out[(int64_t)c * it.n + p] = 0.0;
       continue;
     }
-    double ph[DR][N], dph[DR][N];
+    double ph[DR][N], dph[DR][N] = {};  // dph unused: values only
 #pragma unroll
-    for (int j = 0; j < DR; ++j) lagrange<N, double>(B.z, B.w, it.r[p * DR + j], ph[j], dph[j]);
+    for (int j = 0; j < DR; ++j) lagrange_values<N, double>(B.z, B.w, it.r[p * DR + j], ph[j]);
     for (int c = 0; c < it.nc; ++c) {
       double v;
       map_eval<N, DR, 1, false, double>(it.field + (c * NE + e) * NN, 0, ph, dph, &v, nullptr);
@@ -398,7 +395,7 @@ int launch_tick(fp_server_s* s, TickSlot& t) {
     int* qq = t.queue + off;
     if (s->opts.precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qq + total, 0, sizeof(int), t.st));
     FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision,
-                              0, 5, qq, qq + total, nullptr, t.st));
+                              0, 5, nullptr, qq, qq + total, nullptr, t.st));
     FP_TRY(dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
       constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
       (void)Dc;

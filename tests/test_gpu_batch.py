@@ -110,3 +110,28 @@ def test_batch_rejects_bad_items(fp, torch, config4_small):
     bad = fp.FpBatchItem(5, p.data_ptr(), p.shape[0], 0, 0, 0, 0, None, 0, None)
     with pytest.raises(fp.FindptsError):
         fp.fp_batch_create([meshes[0].handle], [bad])
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_batch_cell_order_invariance(fp, torch, config4_small, precision):
+    """The cell-grouped order of a batch's points leaves every output bit for
+    bit unchanged (plans over meshes set to FP_ORDER_GIVEN take the points
+    as given)."""
+    ws, meshes, pts, oms = config4_small
+    prec = fp.FP_MIXED if precision == "mixed" else fp.FP_F64
+    entries = [(m, torch.from_numpy(p).cuda(), torch.from_numpy(w.field).cuda())
+               for m, p, w in zip(meshes, pts, ws)]
+    outs = []
+    for order in (fp.FP_ORDER_CELL, fp.FP_ORDER_GIVEN):
+        for m in meshes:
+            m.set_point_order(order)
+        b = fp.Batch(entries, prec)
+        b.run()
+        torch.cuda.synchronize()
+        outs.append([[t.clone() for t in o] for o in b.outputs])
+        b.close()
+    for m in meshes:
+        m.set_point_order(fp.FP_ORDER_CELL)
+    for a, b in zip(*outs):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
