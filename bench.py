@@ -265,6 +265,47 @@ def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, peaks):
     return res
 
 
+def projection_block(fp, W, torch, dev, st, flush, args):
+    """Closest-point projection on line elements (the paper's tangential
+    relaxation example, boxes expanded by 100%): a curved closed boundary of
+    2^16 cubic line elements, every node moved along and off the curve
+    (262144 points); find + interpolation of the coordinate field (the
+    closest points), FP64 and mixed precision."""
+    import numpy as np
+    coords = W.star_lines(1 << 16, 3)
+    pts = torch.from_numpy(W.projection_points(coords, np.random.default_rng(7))).to(dev)
+    xc = torch.from_numpy(coords).to(dev)
+    mesh = fp.Mesh(xc, 2, 1, 3, bbox_tol=1.0)
+    n = pts.shape[0]
+    res = {"workload": "star curve, 65536 cubic line elements, 262144 moved nodes, bbox_tol 1.0"}
+    code = torch.empty(n, dtype=torch.int32, device=dev)
+    elem = torch.empty(n, dtype=torch.int32, device=dev)
+    r = torch.empty((n, 1), dtype=torch.float64, device=dev)
+    d2 = torch.empty(n, dtype=torch.float64, device=dev)
+    out = torch.empty((2, n), dtype=torch.float64, device=dev)
+    for prec in ("f64", "mixed"):
+        mesh.set_precision(fp.FP_MIXED if prec == "mixed" else fp.FP_F64)
+        for _ in range(args.warmup):
+            fp.fp_findpts(mesh.handle, pts, code, elem, r, d2)
+            fp.fp_eval(mesh.handle, code, elem, r, xc, 2, out)
+        ts = []
+        for _ in range(max(3, args.steps)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fp.fp_findpts(mesh.handle, pts, code, elem, r, d2)
+            fp.fp_eval(mesh.handle, code, elem, r, xc, 2, out)
+            b.record(st)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        codes = torch.bincount(code.long(), minlength=3).tolist()
+        res[prec] = {"value": n / (statistics.mean(ts) / 1e3), "unit": "points/s", "ms": statistics.mean(ts),
+                     "codes": {"interior": codes[0], "border": codes[1], "not_found": codes[2]}}
+    res["status"] = mesh.device_status()
+    mesh.close()
+    return res
+
+
 def batch_block(fp, W, torch, dev, st, flush, args):
     """The 64-mesh workload (quads, hexes, sphere/torus surfaces, p = 2..7,
     1e3-5e4 elements, 1e3-1e6 points each, scalar fields): one autotuned
@@ -624,6 +665,7 @@ def main():
     mesh.close()
     mixed = None if args.skip_mixed else mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, (peak64, peak32))
     batched = None if (args.skip_batch or rank != 0) else batch_block(fp, W, torch, dev, st, flush, args)
+    projection = None if (args.skip_batch or rank != 0) else projection_block(fp, W, torch, dev, st, flush, args)
     serving = None if (args.skip_serve or rank != 0) else serve_block(fp, W, torch, dev, args)
 
     cpu = None
@@ -648,7 +690,7 @@ def main():
                               "per_point_iterations": float(sv[1]) / n},
             "setup_ms": setup_ms, "wall_s_timed": wall, "device_status": status,
             "e2e": {"value": e2e_v, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "cpu_baseline": cpu, "clocks": clk, "mixed": mixed, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu, "clocks": clk, "mixed": mixed, "batched": batched, "projection": projection, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

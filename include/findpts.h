@@ -271,6 +271,8 @@ typedef struct {
   int precision;         /* FP_F64 or FP_MIXED                                 */
   double tick_timeout_s; /* host watchdog per tick: its requests fail with     */
                          /* FP_ETIMEDOUT (memory kept until the tick ends)     */
+  int64_t tick_points;   /* points per tick: a request's stage is split into   */
+                         /* tiles, the requests with the least work left first */
 } fp_server_opts;
 
 typedef struct {
@@ -279,7 +281,7 @@ typedef struct {
   size_t bytes_in_use;
 } fp_server_stats;
 
-void fp_server_opts_default(fp_server_opts* opts); /* 1 GiB, 64 slots, FP_MIXED, 30 s */
+void fp_server_opts_default(fp_server_opts* opts); /* 1 GiB, 64 slots, FP_MIXED, 30 s, 2^20 */
 
 /* remap_fields[i] ([nc_remap[i]][NE][N^dr], device) and velocity[i]
  * ([d][NE][N^dr], device) may be NULL (arrays themselves may be NULL); they

@@ -321,7 +321,7 @@ FP_REQ_REMAP, FP_REQ_PARTICLE = 0, 1
 
 class FpServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("precision", ctypes.c_int),
-                ("tick_timeout_s", ctypes.c_double)]
+                ("tick_timeout_s", ctypes.c_double), ("tick_points", ctypes.c_int64)]
 
 
 class FpServerStats(ctypes.Structure):
@@ -377,10 +377,11 @@ class Server:
     with fields as device tensors [nc][NE][N^dr]."""
 
     def __init__(self, entries, mem_budget: int = 1 << 30, max_active: int = 64, precision: int = FP_MIXED,
-                 tick_timeout_s: float = 30.0):
+                 tick_timeout_s: float = 30.0, tick_points: int = 1 << 20):
         L = _server_sig()
         o = fp_server_opts_default()
         o.mem_budget, o.max_active, o.precision, o.tick_timeout_s = mem_budget, max_active, precision, tick_timeout_s
+        o.tick_points = tick_points
         n = len(entries)
         self.meshes = [e[0] for e in entries]
         self._keep = entries

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kEvalThreads)
     const int64_t NE = it.m.NE;
     if (c0 == FP_NOT_FOUND || e < 0 || e >= NE) {
       if (c0 != FP_NOT_FOUND) record_status(it.m.status, FP_DEV_BAD_ELEM);
-      for (int c = 0; c < it.nc; ++c) it.out[(int64_t)c * it.n + p] = 0.0;
+      for (int c = 0; c < it.nc; ++c) it.out[(int64_t)c * it.ld + p] = 0.0;
       continue;
     }
     double ph[DR][N], dph[DR][N] = {};  // dph unused: values only
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kEvalThreads)
     for (int c = 0; c < it.nc; ++c) {
       double v;
       map_eval<N, DR, 1, false, double>(it.field + (c * NE + e) * NN, 0, ph, dph, &v, nullptr);
-      it.out[(int64_t)c * it.n + p] = v;
+      it.out[(int64_t)c * it.ld + p] = v;
     }
   }
 }
@@ -239,6 +239,7 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
     bi.field = items[i].field;
     bi.nc = items[i].field ? items[i].nc : 0;
     bi.out = items[i].out;
+    bi.ld = items[i].n;
     if (bi.field) c.has_field = true;
     if (bi.n > 0) {
       bi.cell_base = c.buckets;

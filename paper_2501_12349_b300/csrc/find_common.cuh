@@ -479,7 +479,8 @@ struct BatchItem {
   double* dist2;
   const double* field;
   int nc;
-  double* out;
+  double* out;        // [nc] components, component c at out + c * ld
+  int64_t ld;
   int64_t cell_base;  // first bucket of this item's Psi_L cells in the batch's cell order
 };
 

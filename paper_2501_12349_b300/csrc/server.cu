@@ -8,11 +8,14 @@
 //              particle-tracking algorithm, Sec. 6.7), then a final find of
 //              the end positions.  A particle that leaves the mesh is
 //              NOT_FOUND, its interpolated velocity is 0 and it stays put.
-// A scheduler thread runs ticks.  Each tick takes one stage of every ready
-// request (a request not in the other tick in flight), packs them into batch
-// tables grouped by element shape and issues, on one of two tick streams,
-// one find launch per shape (FP64 or mixed), one eval launch per shape and
-// one particle-advance launch; up to two ticks are in flight.  Requests are
+// A scheduler thread runs ticks.  A tick takes tiles (contiguous ranges of
+// points) of the current stage of the ready requests, those with the least
+// work left in their stage first, up to a budget of points per tick, so a
+// large request proceeds tile by tile while small ones pass it; it packs the
+// tiles into batch tables grouped by element shape and issues, on one of two
+// tick streams, one find launch per shape (FP64 or mixed), one eval launch
+// per shape and one particle-advance launch; up to two ticks are in flight,
+// and a request's stage ends when all its tiles have finished.  Requests are
 // admitted when a first-fit arena inside a fixed device-memory budget and a
 // slot are free; host<->device copies run on a separate copy stream, so
 // arriving requests' uploads and finished requests' downloads overlap the
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(128)
     const int c0 = it.code[p], e = it.elem[p];
     const int64_t NE = it.m.NE;
     if (c0 == FP_NOT_FOUND || e < 0 || e >= NE) {
-      for (int c = 0; c < it.nc; ++c) it.out[(int64_t)c * it.n + p] = 0.0;
+      for (int c = 0; c < it.nc; ++c) it.out[(int64_t)c * it.ld + p] = 0.0;
       continue;
     }
     double ph[DR][N], dph[DR][N] = {};  // dph unused: values only
@@ -71,18 +74,20 @@ __global__ void __launch_bounds__(128)
     for (int c = 0; c < it.nc; ++c) {
       double v;
       map_eval<N, DR, 1, false, double>(it.field + (c * NE + e) * NN, 0, ph, dph, &v, nullptr);
-      it.out[(int64_t)c * it.n + p] = v;
+      it.out[(int64_t)c * it.ld + p] = v;
     }
   }
 }
 
-// One particle stage: mode 0 (midpoint) xs = x + c u; mode 1 (full step)
-// x = x + c u and xs = x.  u is [d][n] from the stage's eval.
+// One particle stage over a tile of a request's points: mode 0 (midpoint)
+// xs = x + c u; mode 1 (full step) x = x + c u and xs = x.  u holds the
+// stage's interpolated velocity, component k at u + k * ld.
 struct AdvItem {
   double* x;
   double* xs;
   const double* u;
   int64_t n;
+  int64_t ld;
   int64_t start;
   double c;
   int mode;
@@ -101,7 +106,7 @@ __global__ void k_advance(const AdvItem* __restrict__ items, int nitems, int64_t
     const AdvItem& it = items[lo];
     const int64_t p = g - it.start;
     for (int c = 0; c < it.d; ++c) {
-      const double v = it.x[p * it.d + c] + it.c * it.u[(int64_t)c * it.n + p];
+      const double v = it.x[p * it.d + c] + it.c * it.u[(int64_t)c * it.ld + p];
       if (it.mode == 0) {
         it.xs[p * it.d + c] = v;
       } else {
@@ -158,7 +163,7 @@ struct Arena {
   }
 };
 
-enum RState { R_QUEUED, R_UPLOADING, R_READY, R_IN_TICK, R_DOWNLOADING, R_DONE };
+enum RState { R_QUEUED, R_UPLOADING, R_READY, R_DOWNLOADING, R_DONE };
 
 struct Request {
   int64_t id;
@@ -171,6 +176,9 @@ struct Request {
   RState state = R_QUEUED;
   int status = FP_OK;
   int stage = 0, nstages = 1;
+  int64_t next = 0;  // first point of the current stage not yet given to a tick
+  int64_t done = 0;  // points of the current stage finished
+  int inflight = 0;  // tiles of this request in ticks on the GPU
   size_t bytes = 0;
   char* block = nullptr;
   double *x = nullptr, *xs = nullptr, *r = nullptr, *dist2 = nullptr, *u = nullptr;
@@ -187,13 +195,19 @@ struct MeshEntry {
   const double* vel;
 };
 
+// A contiguous range of one request's points within one tick.
+struct Tile {
+  int64_t id, off, len;
+};
+
 struct TickSlot {
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
   bool timed_out = false;
+  int fail_rc = 0;  // a launch of this tick failed: its requests fail at completion
   Clock::time_point started;
-  std::vector<int64_t> reqs;
+  std::vector<Tile> tiles;
   BatchItem* items_h = nullptr;  // pinned
   BatchItem* items_d = nullptr;
   AdvItem* adv_h = nullptr;
@@ -212,6 +226,7 @@ struct fp_server_s {
   cudaStream_t copy = nullptr;
   fp::TickSlot slot[2];
   int max_items = 0;
+  int64_t tick_points = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<int64_t> queued;
@@ -323,75 +338,118 @@ void start_download(fp_server_s* s, Request& q) {
   q.state = R_DOWNLOADING;
 }
 
-// Builds and launches one tick on slot t from the ready requests (lock held).
+// (first item, items, points, queue offset, element shape, a mesh of the shape)
+using TickLaunch = std::tuple<int, int, int64_t, int64_t, std::tuple<int, int, int>, const fp_mesh_s*>;
+int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& launches, int ni, int na,
+                 int64_t atotal);
+
+// Builds one tick on slot t from the ready requests and launches it (lock
+// held).  Returns 0 (nothing to do, or launched), or a negative status.
 int launch_tick(fp_server_s* s, TickSlot& t) {
-  t.reqs.clear();
+  t.tiles.clear();
+  // tile-level interleaving: the requests with the least work left in their
+  // current stage go first, each takes what the tick's point budget leaves
+  std::vector<std::pair<int64_t, int64_t>> cand;  // (points left, id)
   for (auto& kv : s->reqs) {
-    Request& q = *kv.second;
-    if (q.state == R_READY && (int)t.reqs.size() < s->max_items) t.reqs.push_back(q.id);
+    const Request& q = *kv.second;
+    if (q.state == R_READY && q.status == FP_OK && q.next < q.n) cand.emplace_back(q.n - q.next, q.id);
   }
-  if (t.reqs.empty()) return 0;
-  std::sort(t.reqs.begin(), t.reqs.end());
+  if (cand.empty()) return 0;
+  std::sort(cand.begin(), cand.end());
+  int64_t budget = s->tick_points;
+  for (auto& c : cand) {
+    if (budget <= 0 || (int)t.tiles.size() >= s->max_items) break;
+    const Request& q = *s->reqs[c.second];
+    const int64_t len = std::min(q.n - q.next, budget);
+    t.tiles.push_back({q.id, q.next, len});
+    budget -= len;
+  }
   // group by element shape
-  std::map<std::tuple<int, int, int>, std::vector<int64_t>> cls;
-  for (int64_t id : t.reqs) {
-    const Request& q = *s->reqs[id];
+  std::map<std::tuple<int, int, int>, std::vector<int>> cls;
+  for (int k = 0; k < (int)t.tiles.size(); ++k) {
+    const Request& q = *s->reqs[t.tiles[k].id];
     const fp_mesh_s* m = s->meshes[q.mesh].m;
-    cls[std::make_tuple(m->N, m->d, m->dr)].push_back(id);
+    cls[std::make_tuple(m->N, m->d, m->dr)].push_back(k);
   }
   int ni = 0, na = 0;
   int64_t qoff = 0, atotal = 0;
-  std::vector<std::tuple<int, int, int64_t, int64_t, std::tuple<int, int, int>>> launches;
+  std::vector<TickLaunch> launches;
   for (auto& kv : cls) {
     const int first = ni;
     int64_t total = 0;
-    for (int64_t id : kv.second) {
-      Request& q = *s->reqs[id];
+    const fp_mesh_s* m0 = nullptr;
+    for (int k : kv.second) {
+      const Tile& tl = t.tiles[k];
+      Request& q = *s->reqs[tl.id];
       const MeshEntry& me = s->meshes[q.mesh];
+      const int d = me.m->d, dr = me.m->dr;
+      if (!m0) m0 = me.m;
       BatchItem& bi = t.items_h[ni++];
       memset(&bi, 0, sizeof(bi));
       bi.m = me.m->view();
-      bi.pts = q.xs;
-      bi.n = q.n;
+      bi.pts = q.xs + tl.off * d;
+      bi.n = tl.len;
       bi.start = total;
-      bi.code = q.code;
-      bi.elem = q.elem;
-      bi.r = q.r;
-      bi.dist2 = q.dist2;
+      bi.code = q.code + tl.off;
+      bi.elem = q.elem + tl.off;
+      bi.r = q.r + tl.off * dr;
+      bi.dist2 = q.dist2 + tl.off;
       const bool last = q.stage == q.nstages - 1;
       if (q.kind == FP_REQ_REMAP) {
         bi.field = me.remap_field;
         bi.nc = me.remap_field ? me.nc_remap : 0;
       } else if (!last) {
         bi.field = me.vel;
-        bi.nc = me.m->d;
+        bi.nc = d;
       }
-      bi.out = q.u;
-      total += q.n;
+      bi.out = q.u + tl.off;
+      bi.ld = q.n;
+      total += tl.len;
       if (q.kind == FP_REQ_PARTICLE && !last) {
         AdvItem& a = t.adv_h[na++];
-        a.x = q.x;
-        a.xs = q.xs;
-        a.u = q.u;
-        a.n = q.n;
+        a.x = q.x + tl.off * d;
+        a.xs = q.xs + tl.off * d;
+        a.u = q.u + tl.off;
+        a.n = tl.len;
+        a.ld = q.n;
         a.start = atotal;
         a.mode = (q.stage % 2 == 0) ? 0 : 1;
         a.c = (q.stage % 2 == 0) ? 0.5 * q.dt : q.dt;
-        a.d = me.m->d;
-        atotal += q.n;
+        a.d = d;
+        atotal += tl.len;
       }
     }
-    launches.emplace_back(first, ni - first, total, qoff, kv.first);
+    launches.emplace_back(first, ni - first, total, qoff, kv.first, m0);
     qoff += total + 1;
   }
-  if (qoff > t.queue_cap) return FP_ENOMEM;
+  if (qoff > t.queue_cap) return FP_ENOMEM;  // nothing launched; the caller fails t.tiles
+  // from here on the tiles belong to this tick: a failure below still
+  // completes through t.done, so no request memory is released while
+  // kernels that were launched may use it
+  for (const Tile& tl : t.tiles) {
+    Request& q = *s->reqs[tl.id];
+    q.next += tl.len;
+    ++q.inflight;
+  }
+  t.busy = true;
+  t.fail_rc = FP_OK;
+  t.started = Clock::now();
+  s->stats.ticks++;
+  const int rc = enqueue_tick(s, t, launches, ni, na, atotal);
+  if (rc != FP_OK) t.fail_rc = rc;
+  if (cudaEventRecord(t.done, t.st) != cudaSuccess && t.fail_rc == FP_OK) t.fail_rc = FP_ELAUNCH;
+  return rc;
+}
+
+int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& launches, int ni, int na,
+                 int64_t atotal) {
   FP_CUDA_TRY(cudaMemcpyAsync(t.items_d, t.items_h, sizeof(BatchItem) * ni, cudaMemcpyHostToDevice, t.st));
   if (na) FP_CUDA_TRY(cudaMemcpyAsync(t.adv_d, t.adv_h, sizeof(AdvItem) * na, cudaMemcpyHostToDevice, t.st));
   for (auto& L : launches) {
     const int first = std::get<0>(L), cnt = std::get<1>(L);
     const int64_t total = std::get<2>(L), off = std::get<3>(L);
     const int N = std::get<0>(std::get<4>(L)), d = std::get<1>(std::get<4>(L)), dr = std::get<2>(std::get<4>(L));
-    const fp_mesh_s* m0 = s->meshes[s->reqs[cls[std::get<4>(L)][0]]->mesh].m;
+    const fp_mesh_s* m0 = std::get<5>(L);
     int* qq = t.queue + off;
     if (s->opts.precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qq + total, 0, sizeof(int), t.st));
     FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision,
@@ -408,29 +466,30 @@ int launch_tick(fp_server_s* s, TickSlot& t) {
     k_advance<<<grid_for(atotal, 256, sm_count() * 8), 256, 0, t.st>>>(t.adv_d, na, atotal);
     FP_CUDA_TRY(cudaGetLastError());
   }
-  FP_CUDA_TRY(cudaEventRecord(t.done, t.st));
-  for (int64_t id : t.reqs) s->reqs[id]->state = R_IN_TICK;
-  t.busy = true;
-  t.started = Clock::now();
-  s->stats.ticks++;
-  return 0;
+  return FP_OK;
 }
 
-// Tick t finished (lock held): advance the stages of its requests.
+// Tick t finished (lock held): count its tiles; a request whose current
+// stage is complete moves to the next stage or to its download.
 void complete_tick(fp_server_s* s, TickSlot& t, int status) {
-  for (int64_t id : t.reqs) {
-    auto f = s->reqs.find(id);
+  for (const Tile& tl : t.tiles) {
+    auto f = s->reqs.find(tl.id);
     if (f == s->reqs.end()) continue;
     Request& q = *f->second;
-    if (status != FP_OK || q.status != FP_OK) {
-      finish(s, q, status);
+    --q.inflight;
+    q.done += tl.len;
+    if (status != FP_OK && q.status == FP_OK) q.status = status;
+    if (q.inflight > 0) continue;  // memory in use by the other tick
+    if (q.status != FP_OK) {
+      finish(s, q, q.status);
       continue;
     }
+    if (q.done < q.n) continue;
     ++q.stage;
+    q.next = q.done = 0;
     if (q.stage >= q.nstages) start_download(s, q);
-    else q.state = R_READY;
   }
-  t.reqs.clear();
+  t.tiles.clear();
   t.busy = false;
   t.timed_out = false;
 }
@@ -464,20 +523,25 @@ void worker_loop(fp_server_s* s) {
         if (!t.timed_out && Clock::now() - t.started > tick_limit) {
           t.timed_out = true;
           s->stats.timeouts++;
-          for (int64_t id : t.reqs) s->reqs[id]->status = FP_ETIMEDOUT;
+          for (const Tile& tl : t.tiles) s->reqs[tl.id]->status = FP_ETIMEDOUT;
         }
         continue;
       }
-      complete_tick(s, t, e == cudaSuccess ? FP_OK : FP_ELAUNCH);
+      complete_tick(s, t, e != cudaSuccess ? FP_ELAUNCH : t.fail_rc);
       progressed = true;
     }
     // launch new ticks on free slots
     for (auto& t : s->slot) {
       if (t.busy) continue;
       const int rc = launch_tick(s, t);
-      if (rc < 0) {
-        for (int64_t id : t.reqs) finish(s, *s->reqs[id], rc);
-        t.reqs.clear();
+      if (rc < 0 && !t.busy) {
+        // nothing was launched (no queue room): fail the requests it picked
+        for (const Tile& tl : t.tiles) {
+          Request& q = *s->reqs[tl.id];
+          if (q.status == FP_OK) q.status = rc;
+          if (q.inflight == 0 && q.state != R_DONE) finish(s, q, rc);
+        }
+        t.tiles.clear();
       } else if (t.busy) {
         progressed = true;
       }
@@ -527,6 +591,7 @@ extern "C" void fp_server_opts_default(fp_server_opts* o) {
   o->max_active = 64;
   o->precision = FP_MIXED;
   o->tick_timeout_s = 30.0;
+  o->tick_points = (int64_t)1 << 20;
 }
 
 extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* const* remap_fields,
@@ -539,7 +604,8 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
   fp_server_opts o;
   fp_server_opts_default(&o);
   if (opts) o = *opts;
-  if (o.mem_budget < ((size_t)1 << 20) || o.max_active < 1 || (o.precision != FP_F64 && o.precision != FP_MIXED))
+  if (o.mem_budget < ((size_t)1 << 20) || o.max_active < 1 || (o.precision != FP_F64 && o.precision != FP_MIXED) ||
+      o.tick_points < 1)
     return FP_EINVAL;
   for (int i = 0; i < nm; ++i) {
     if (!meshes[i]) return FP_EINVAL;
@@ -553,6 +619,7 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
     s->meshes.push_back({meshes[i], remap_fields ? remap_fields[i] : nullptr,
                          (remap_fields && remap_fields[i]) ? nc_remap[i] : 0, velocity ? velocity[i] : nullptr});
   s->max_items = o.max_active;
+  s->tick_points = o.tick_points;
   // bytes per point >= 72, so the budget bounds the points in flight
   const int64_t qcap = (int64_t)(o.mem_budget / 72) + 2 * 64 + 16;
   int rc = FP_OK;

@@ -167,3 +167,31 @@ def test_wait_timeout_and_cancel(fp, torch, resident):
     s.wait(big, timeout_s=120)
     assert s.stats().timeouts == 0
     s.close()
+
+
+def test_tiles_small_ticks(fp, torch, resident):
+    """With a point budget of 1000 per tick every stage is split into many
+    tiles (tile-level interleaving): results equal those of the default
+    budget, and a small request submitted after a large one finishes first."""
+    rng = np.random.default_rng(56)
+    pa = rng.uniform(-0.02, 1.02, (30000, 3))
+    pp = rng.uniform(0.05, 0.95, (8000, 3))
+    s0 = server_of(fp, resident)
+    ref_a = [a.copy() for a in s0.wait(s0.submit(1, fp.FP_REQ_REMAP, pa))]
+    ref_p = [a.copy() for a in s0.wait(s0.submit(2, fp.FP_REQ_PARTICLE, pp, rk_steps=2, dt=0.01))]
+    s0.close()
+    s = server_of(fp, resident, tick_points=1000)
+    big = s.submit(0, fp.FP_REQ_PARTICLE, rng.uniform(0.05, 0.95, (200000, 3)), rk_steps=4, dt=0.001)
+    small = s.submit(1, fp.FP_REQ_REMAP, rng.uniform(0, 1, (200, 3)))
+    s.wait(small, timeout_s=60)
+    done_big, _ = s.poll(big)
+    assert not done_big  # the small request passed the large one
+    got_a = s.wait(s.submit(1, fp.FP_REQ_REMAP, pa))
+    got_p = s.wait(s.submit(2, fp.FP_REQ_PARTICLE, pp, rk_steps=2, dt=0.01))
+    for a, b in zip(ref_a, got_a):
+        assert np.array_equal(a, b)
+    for a, b in zip(ref_p, got_p):
+        assert np.array_equal(a, b)
+    s.wait(big, timeout_s=120)
+    assert s.stats().ticks > 60
+    s.close()
