@@ -338,3 +338,41 @@ def test_distributed_find_single_rank_nccl(fp, torch):
         m.close()
     finally:
         dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("variant", ["offset_scaled", "strong_deformation", "single_element"])
+def test_robustness_cases(fp, torch, variant, precision):
+    """Meshes far from the origin and scaled (the FP32 prefilters work on
+    coordinates relative to each element, so they must keep their rounding
+    margins there), strongly deformed elements (ill-conditioned Jacobians,
+    which the mixed path hands to FP64), and a one-element mesh; points at
+    interior GLL nodes (the closest-node start is the answer) included."""
+    rng = np.random.default_rng(16)
+    if variant == "offset_scaled":
+        coords = W.hex_mesh(5, 4, 0.3) * 3.7 + np.array([1000.0, -2000.0, 500.0])[:, None, None]
+        lo, hi = np.array([1000.0, -2000.0, 500.0]) - 0.1, np.array([1000.0, -2000.0, 500.0]) + 3.8
+    elif variant == "strong_deformation":
+        coords = W.hex_mesh(5, 4, 0.45)  # diagonally dominant Jacobian: still bijective
+        lo, hi = np.full(3, -0.05), np.full(3, 1.05)
+    else:
+        coords = W.hex_mesh(1, 5, 0.3)
+        lo, hi = np.full(3, -0.1), np.full(3, 1.1)
+    order = int(round(coords.shape[2] ** (1 / 3))) - 1
+    N = order + 1
+    om = oracle.OracleMesh(coords, 3, 3, N)
+    pts = rng.uniform(lo, hi, (15000, 3))
+    z = W.gll_points(N)[1:-1]
+    el = rng.integers(0, om.NE, 500).astype(np.int32)
+    rn = z[rng.integers(0, z.size, (500, 3))]
+    pts = np.concatenate([pts, om.forward_map(el, rn)])
+    m = gpu_mesh(fp, torch, coords, 3, 3, order)
+    m.set_precision(fp.FP_MIXED if precision == "mixed" else fp.FP_F64)
+    g = gpu_find(torch, m, pts)
+    o = om.findpts(pts)
+    xs = float(np.abs(coords).max())
+    compare_find(o, g, label=f"{variant} {precision}", xscale=1.3 * xs)
+    assert np.all(g[0][-500:] == 0)
+    np.testing.assert_allclose(g[2][-500:], rn, atol=1e-10)
+    assert m.device_status() == 0
+    m.close()
