@@ -18,6 +18,7 @@ rank's time).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -95,9 +96,11 @@ def mixed_flop_model(stats, N, d, dr):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms; the sampler
+    starts before the warm-up (nvidia-smi takes a while to start) and only the
+    samples whose timestamps fall inside the timed region are kept."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -105,15 +108,23 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.f = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark(self, begin: bool):
+        """Marks the start (begin) or the end of the timed region."""
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -126,21 +137,27 @@ class ClockSampler:
         self.f.flush()
         rows = [l.split(",") for l in Path(self.f.name).read_text().splitlines() if l.strip()]
         os.unlink(self.f.name)
-        sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        parsed = []
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                mx = max(mx, float(r[2]))
-                for nm, v in zip(names, r[5:9]):
-                    if v.strip().lower() == "active":
-                        reasons.add(nm)
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                parsed.append((ts, float(r[2]), float(r[3]),
+                               [nm for nm, v in zip(names, r[6:10]) if v.strip().lower() == "active"]))
             except (ValueError, IndexError):
                 continue
-        if not sm:
+        if not parsed:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        window = "timed region"
+        sel = [p for p in parsed if self.t0 is not None and self.t1 is not None and self.t0 <= p[0] <= self.t1]
+        if not sel:  # the region was shorter than the sampling interval
+            window = "nearest sample"
+            mid = 0.5 * ((self.t0 or 0) + (self.t1 or 0))
+            sel = [min(parsed, key=lambda p: abs(p[0] - mid))]
+        reasons = sorted({nm for p in sel for nm in p[3]})
+        return {"sm_mhz": statistics.median(p[1] for p in sel), "sm_max_mhz": max(p[2] for p in sel),
+                "reasons": reasons, "samples": len(sel), "window": window,
+                "samples_total": len(parsed)}
 
 
 def cpu_baseline(w, nc_field, target_s=10.0):
@@ -576,16 +593,18 @@ def main():
         fp.fp_findpts(mesh.handle, pts, code, elem, r, dist2)
         fp.fp_eval(mesh.handle, code, elem, r, field, 1, out)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
+    time.sleep(0.3)  # nvidia-smi is sampling by now
 
-    clocks = ClockSampler(local)
-    clocks.start()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
+    clocks.mark(True)
     wall0 = time.perf_counter()
     for s in range(args.steps):
         flush.zero_()
@@ -595,6 +614,7 @@ def main():
         fp.fp_eval(mesh.handle, code, elem, r, field, 1, out)
         ev[s][2].record(st)
     torch.cuda.synchronize()
+    clocks.mark(False)
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -680,7 +700,10 @@ def main():
             "config": {"workload": WORKLOAD, "points_per_gpu": n, "precision": args.precision,
                        "nc": 1, "l2": "flushed (256 MB write) before each timed step",
                        "parallelism": f"replicas{world}"},
-            "gpu_launches": 2 * args.steps,
+            # per step: the cell order (k_point_cells, k_scan, k_point_scatter),
+            # the find (k_find_f64; mixed: k_find_mixed + k_find_f64 on the
+            # handed-over points) and k_eval_f64
+            "gpu_launches": (5 if args.precision == "f64" else 6) * args.steps,
             "roofline": roofline,
             "kernels_ms": {"find": statistics.mean(find_ms), "eval": statistics.mean(eval_ms)},
             "eval_roofline": {"bound": "alu", "achieved": fl_eval / eval_avg / 1e12, "peak": peak64,
