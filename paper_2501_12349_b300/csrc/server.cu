@@ -214,6 +214,8 @@ struct TickSlot {
   AdvItem* adv_d = nullptr;
   int* queue = nullptr;
   int64_t queue_cap = 0;
+  int* order = nullptr;  // cell-order scratch of one shape's tiles
+  int64_t order_cap = 0;
 };
 
 }  // namespace
@@ -338,8 +340,9 @@ void start_download(fp_server_s* s, Request& q) {
   q.state = R_DOWNLOADING;
 }
 
-// (first item, items, points, queue offset, element shape, a mesh of the shape)
-using TickLaunch = std::tuple<int, int, int64_t, int64_t, std::tuple<int, int, int>, const fp_mesh_s*>;
+// (first item, items, points, queue offset, element shape, a mesh of the
+// shape, cell-order buckets)
+using TickLaunch = std::tuple<int, int, int64_t, int64_t, std::tuple<int, int, int>, const fp_mesh_s*, int64_t>;
 int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& launches, int ni, int na,
                  int64_t atotal);
 
@@ -378,15 +381,24 @@ int launch_tick(fp_server_s* s, TickSlot& t) {
     const int first = ni;
     int64_t total = 0;
     const fp_mesh_s* m0 = nullptr;
+    // cell order: one range of buckets per mesh, shared by all its tiles,
+    // so points of different requests in one cell are searched together
+    std::map<int, int64_t> base;
+    int64_t buckets = 0;
     for (int k : kv.second) {
       const Tile& tl = t.tiles[k];
       Request& q = *s->reqs[tl.id];
       const MeshEntry& me = s->meshes[q.mesh];
       const int d = me.m->d, dr = me.m->dr;
       if (!m0) m0 = me.m;
+      if (!base.count(q.mesh)) {
+        base[q.mesh] = buckets;
+        buckets += me.m->ncell + 1;
+      }
       BatchItem& bi = t.items_h[ni++];
       memset(&bi, 0, sizeof(bi));
       bi.m = me.m->view();
+      bi.cell_base = base[q.mesh];
       bi.pts = q.xs + tl.off * d;
       bi.n = tl.len;
       bi.start = total;
@@ -419,7 +431,7 @@ int launch_tick(fp_server_s* s, TickSlot& t) {
         atotal += tl.len;
       }
     }
-    launches.emplace_back(first, ni - first, total, qoff, kv.first, m0);
+    launches.emplace_back(first, ni - first, total, qoff, kv.first, m0, buckets);
     qoff += total + 1;
   }
   if (qoff > t.queue_cap) return FP_ENOMEM;  // nothing launched; the caller fails t.tiles
@@ -450,10 +462,15 @@ int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& lau
     const int64_t total = std::get<2>(L), off = std::get<3>(L);
     const int N = std::get<0>(std::get<4>(L)), d = std::get<1>(std::get<4>(L)), dr = std::get<2>(std::get<4>(L));
     const fp_mesh_s* m0 = std::get<5>(L);
+    const int64_t buckets = std::get<6>(L);
     int* qq = t.queue + off;
     if (s->opts.precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qq + total, 0, sizeof(int), t.st));
+    // the shapes run one after another on t.st, so they share the scratch
+    int* order = nullptr;
+    if (total >= (1 << 14) && 2 * total + 2 * buckets + 1 <= t.order_cap)
+      FP_TRY(batch_cell_order(t.items_d + first, cnt, total, d, buckets, t.order, &order, t.st));
     FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision,
-                              0, 5, nullptr, qq, qq + total, nullptr, t.st));
+                              0, 5, order, qq, qq + total, nullptr, t.st));
     FP_TRY(dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
       constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
       (void)Dc;
@@ -575,6 +592,7 @@ void destroy_server(fp_server_s* s) {
     cudaFree(t.items_d);
     cudaFree(t.adv_d);
     cudaFree(t.queue);
+    cudaFree(t.order);
   }
   for (auto& kv : s->reqs)
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
@@ -622,12 +640,16 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
   s->tick_points = o.tick_points;
   // bytes per point >= 72, so the budget bounds the points in flight
   const int64_t qcap = (int64_t)(o.mem_budget / 72) + 2 * 64 + 16;
+  int64_t all_buckets = 0;
+  for (auto& me : s->meshes) all_buckets += me.m->ncell + 1;
+  const int64_t ocap = 2 * std::min(qcap, o.tick_points) + 2 * all_buckets + 1;
   int rc = FP_OK;
   if (!s->arena.init(o.mem_budget)) rc = FP_ENOMEM;
   if (rc == FP_OK && cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess) rc = FP_ELAUNCH;
   for (auto& t : s->slot) {
     if (rc != FP_OK) break;
     t.queue_cap = qcap;
+    t.order_cap = ocap;
     if (cudaStreamCreateWithFlags(&t.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&t.items_h, sizeof(BatchItem) * s->max_items) != cudaSuccess ||
@@ -635,7 +657,8 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
       rc = FP_ELAUNCH;
     else if (cudaMalloc(&t.items_d, sizeof(BatchItem) * s->max_items) != cudaSuccess ||
              cudaMalloc(&t.adv_d, sizeof(AdvItem) * s->max_items) != cudaSuccess ||
-             cudaMalloc(&t.queue, sizeof(int) * qcap) != cudaSuccess)
+             cudaMalloc(&t.queue, sizeof(int) * qcap) != cudaSuccess ||
+             cudaMalloc(&t.order, sizeof(int) * ocap) != cudaSuccess)
       rc = FP_ENOMEM;
   }
   if (rc != FP_OK) {
