@@ -97,6 +97,14 @@ def num_threads() -> int:
     return lib().or_num_threads()
 
 
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of later oracle calls."""
+    f = lib().or_set_num_threads
+    f.argtypes = [_int]
+    f.restype = None
+    f(int(n))
+
+
 def gll_nodes(N: int) -> np.ndarray:
     z = np.zeros(N)
     assert lib().or_gll_nodes(N, _p(z)) == 0

@@ -1037,3 +1037,8 @@ int or_forward_map(const double* coords, int d, int dr, int N, int64_t NE,
 }
 
 int or_num_threads(void) { return omp_get_max_threads(); }
+
+/* Sets the OpenMP thread count of later calls (n >= 1). */
+void or_set_num_threads(int n) {
+  if (n >= 1) omp_set_num_threads(n);
+}
