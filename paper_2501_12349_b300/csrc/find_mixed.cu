@@ -32,7 +32,8 @@ namespace {
 enum : int { X_IDLE = 0, X_SCAN = 1, X_NEWTON = 2, X_RESTORE = 3, X_PARK = 4, X_DONE = 5 };
 enum : int { X_INIT = 1, X_TRIAL = 2, X_REST = 3 };
 
-constexpr float kTol32 = 2e-6f;    // FP32 phase: stop when |dr|_inf < kTol32
+constexpr float kTol32 = 1e-4f;    // FP32 phase: stop when |dr|_inf < kTol32 (the step taken
+                                   // then leaves an error near the FP32 floor)
 constexpr float kTau32 = 1e-5f;    // FP32 rounding-level acceptance factor
 constexpr float kBorder32 = 1e-4f; // "clearly outside": distance > kBorder32 * Xrel
 constexpr int kPark = 28;          // run the FP64 refinement with >= kPark lanes parked
