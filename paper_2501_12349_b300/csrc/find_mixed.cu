@@ -36,7 +36,7 @@ constexpr float kTol32 = 1e-4f;    // FP32 phase: stop when |dr|_inf < kTol32 (t
                                    // then leaves an error near the FP32 floor)
 constexpr float kTau32 = 1e-5f;    // FP32 rounding-level acceptance factor
 constexpr float kBorder32 = 1e-4f; // "clearly outside": distance > kBorder32 * Xrel
-constexpr int kPark = 28;          // run the FP64 refinement with >= kPark lanes parked
+constexpr int kPark = 31;          // run the FP64 refinement with >= kPark lanes parked
 constexpr int kMaxRefine = 4;
 
 // The FP64 kernel that finishes the queued points counts into the second
