@@ -225,8 +225,9 @@ int fp_batch_run(fp_batch b, void* stream);
 
 /* The launch shape autotuner: for every element shape of the plan, times the
  * shape's launches for CTAs per SM (the kernel's register-limited maximum
- * and one fewer: {2, 3} for FP_MIXED and for FP_F64 up to order 5, {1, 2}
- * for FP_F64 at orders 6 and 7) and points per CTA chunk in {32, 128, 512} on the plan's own data (best of two timed runs each), keeps
+ * and one fewer: for FP_F64 {2, 3} up to order 5 and {1, 2} above; for
+ * FP_MIXED {3, 4} or {2, 3} by element shape) and points per CTA chunk in
+ * {32, 128, 512} on the plan's own data (best of two timed runs each), keeps
  * the fastest, records it for later plans and re-captures the graph.
  * Overwrites the plan's outputs.  Synchronous. */
 int fp_batch_autotune(fp_batch b, void* stream);

@@ -316,7 +316,7 @@ extern "C" int fp_batch_autotune(fp_batch b, void* stream) {
     if (c.total == 0 || rc != FP_OK) continue;
     Tuning best;
     // CTAs per SM: the kernel's register-limited maximum and one fewer
-    const int cmax = b->precision == FP_MIXED ? 3 : f64_ctas(c.N);
+    const int cmax = b->precision == FP_MIXED ? mixed_ctas(c.N, c.d, c.dr) : f64_ctas(c.N);
     const int ctas[2] = {cmax - 1, cmax};
     for (int a = 0; a < 2 && rc == FP_OK; ++a)
       for (int k = 0; k < 3 && rc == FP_OK; ++k) {
@@ -358,7 +358,8 @@ extern "C" int fp_batch_describe(fp_batch b, int i, fp_batch_class_info* info) {
   info->n_items = (int)c.items.size();
   info->n_points = c.total;
   info->ctas_per_sm = c.tune.ctas_per_sm > 0 ? c.tune.ctas_per_sm
-                                             : (b->precision == FP_MIXED ? 3 : fp::f64_ctas(c.N));
+                                             : (b->precision == FP_MIXED ? fp::mixed_ctas(c.N, c.d, c.dr)
+                                                                          : fp::f64_ctas(c.N));
   info->chunk_points = 1 << c.tune.clog2;
   info->tuned_ms = c.tune.ms;
   return FP_OK;

@@ -35,6 +35,15 @@ struct Counters {
 // CTAs of kFindThreads per SM that the FP64 find kernel is compiled for:
 // its registers fit three per SM up to N = 6 and two above.
 __host__ __device__ constexpr int f64_ctas(int N) { return N <= 6 ? 3 : 2; }
+// The same for the mixed-precision kernel: four per SM where its registers
+// fit 128 without spilling, three elsewhere (surface quads of N >= 5, whose
+// FP64 refinement also evaluates G, and hexes of N >= 7), two for surface
+// quads of N = 8.
+__host__ __device__ constexpr int mixed_ctas(int N, int D, int DR) {
+  return (DR == 3 && N <= 6) || (DR == 2 && (D == 2 || N <= 4)) || DR == 1 ? 4
+         : (D == 3 && DR == 2 && N >= 8)                                ? 2
+                                                                         : 3;
+}
 
 inline int sm_count() {
   static int n = 0;

@@ -333,10 +333,8 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
   cnt.flush(stats);
 }
 
-constexpr int kMixedCtasPerSm = 3;
-
 template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
+__global__ void __launch_bounds__(kFindThreads, mixed_ctas(N, D, DR))
     k_find_mixed(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
                  const int* __restrict__ pidx, int64_t n, int* __restrict__ code, int* __restrict__ elem,
                  double* __restrict__ rout, double* __restrict__ dist2, int* __restrict__ queue,
@@ -346,7 +344,7 @@ __global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
 }
 
 template <int N, int D, int DR>
-__global__ void __launch_bounds__(kFindThreads, kMixedCtasPerSm)
+__global__ void __launch_bounds__(kFindThreads, mixed_ctas(N, D, DR))
     k_find_mixed_batch(const BatchItem* __restrict__ items, int nitems, int64_t total,
                        const int* __restrict__ gidx, const BasisTab B, int* __restrict__ queue,
                        int* __restrict__ qcount, int clog2, unsigned long long* stats) {
@@ -368,7 +366,7 @@ int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pi
   const DevMesh v = m->view();
   return dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
-    k_find_mixed<N, D, DR><<<persistent_blocks(n, kMixedCtasPerSm), kFindThreads, 0, st>>>(
+    k_find_mixed<N, D, DR><<<persistent_blocks(n, mixed_ctas(N, D, DR)), kFindThreads, 0, st>>>(
         v, m->basis, pts, pidx, n, code, elem, r, dist2, queue, qcount, stats);
     k_find_f64<N, D, DR><<<persistent_blocks(n, f64_ctas(N)), kFindThreads, 0, st>>>(
         v, m->basis, pts, queue, n, qcount, code, elem, r, dist2, fallback_stats(stats));
@@ -387,7 +385,7 @@ int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N,
                        int* queue, int* qcount, unsigned long long* stats, cudaStream_t st) {
   return dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int NN = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
-    if (ctas_per_sm <= 0) ctas_per_sm = precision == FP_MIXED ? kMixedCtasPerSm : f64_ctas(NN);
+    if (ctas_per_sm <= 0) ctas_per_sm = precision == FP_MIXED ? mixed_ctas(NN, D, DR) : f64_ctas(NN);
     const int blocks = persistent_blocks(total, ctas_per_sm);
     if (precision == FP_MIXED) {
       k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, order, B, queue,
