@@ -209,6 +209,101 @@ __device__ int closest_node(const DevMesh& m, int e, const double (&xs)[D], cons
   return nb;
 }
 
+// closest_node for every lane of a converged warp that wants it, the whole
+// warp on one request at a time: lane l scans nodes l, l + 32, ... (loads
+// coalesced across the warp), and a butterfly merges the lanes' best two
+// (distance, node) pairs, ties to the lowest node index; the certification
+// and the FP64 fallback are those of closest_node, the fallback scan shared
+// the same way.  Returns the owner's node in nb.
+template <int N, int D, int DR>
+__device__ void closest_node_warp(bool want, const DevMesh& m, int e, const double (&xs)[D], const float (&xr)[D],
+                                  int& nb) {
+  constexpr int NN = ipow(N, DR);
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned mask = __ballot_sync(kAll, want);
+  // this lane's request data, broadcast below
+  const float* X32m = m.coords32 + (int64_t)e * NN;
+  const double* X64m = m.coords + (int64_t)e * NN;
+  float xm = 0.f;
+#pragma unroll
+  for (int c = 0; c < D; ++c) xm = fmaxf(xm, fabsf(xr[c]));
+  const float Em = want ? 2.3841858e-07f * (xm + __ldg(m.box32 + (int64_t)e * BOX32 + 18)) : 0.f;
+  while (mask) {
+    const int src = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const float* X32 = reinterpret_cast<const float*>(
+        __shfl_sync(kAll, reinterpret_cast<unsigned long long>(X32m), src));
+    const int64_t cs = __shfl_sync(kAll, (long long)m.cstride, src);
+    float r32[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) r32[c] = __shfl_sync(kAll, xr[c], src);
+    float b1 = INFINITY, b2 = INFINITY;
+    int i1 = NN;
+    for (int n = lane; n < NN; n += 32) {
+      float d = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const float t = r32[c] - __ldg(X32 + c * cs + n);
+        d = fmaf(t, t, d);
+      }
+      if (d < b1) {  // nodes ascend per lane: ties keep the lower index
+        b2 = b1;
+        b1 = d;
+        i1 = n;
+      } else if (d < b2) {
+        b2 = d;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob1 = __shfl_xor_sync(kAll, b1, o), ob2 = __shfl_xor_sync(kAll, b2, o);
+      const int oi1 = __shfl_xor_sync(kAll, i1, o);
+      const bool other = ob1 < b1 || (ob1 == b1 && oi1 < i1);
+      const float lo = other ? ob1 : b1, hi = other ? b1 : ob1;
+      b2 = fminf(hi, fminf(b2, ob2));
+      b1 = lo;
+      i1 = other ? oi1 : i1;
+    }
+    const float E = __shfl_sync(kAll, Em, src);
+    const float B1 = 2.f * sqrtf(D * b1) * E + D * E * E + 4.7683716e-07f * b1;
+    const float B2 = 2.f * sqrtf(D * b2) * E + D * E * E + 4.7683716e-07f * b2;
+    int best_n = i1;
+    if (!(b2 - B2 > b1 + B1)) {  // uncertified: the FP64 scan decides
+      const double* X = reinterpret_cast<const double*>(
+          __shfl_sync(kAll, reinterpret_cast<unsigned long long>(X64m), src));
+      double x64[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) x64[c] = __shfl_sync(kAll, xs[c], src);
+      double best = INFINITY;
+      int bi = NN;
+      for (int n = lane; n < NN; n += 32) {
+        double dd = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const double t = __dsub_rn(x64[c], __ldg(X + c * cs + n));
+          dd = __dadd_rn(dd, __dmul_rn(t, t));
+        }
+        if (dd < best) {
+          best = dd;
+          bi = n;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(kAll, best, o);
+        const int oi = __shfl_xor_sync(kAll, bi, o);
+        if (ob < best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      best_n = bi;
+    }
+    if (lane == src) nb = best_n;
+  }
+}
+
 template <int N, int DR, typename T>
 __device__ __forceinline__ void node_coords(const BasisTab& B, int n, T (&r)[DR]) {
   const int idx[3] = {n % N, (n / N) % N, n / (N * N)};

@@ -101,11 +101,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
         }
         ++cnt.v[0];
         xscale = aabb_scale<D>(*mp, e);
-        float xr[D];
-        rel_point<D>(*mp, e, xs, xr);
-        const int nb = closest_node<N, D, DR>(*mp, e, xs, xr);
-        node_coords<N, DR>(B, nb, r);
-        etype = E_INIT;
+        etype = E_INIT;  // the start r0, the closest node, is found by the warp below
         need = true;
         break;
       }
@@ -167,6 +163,15 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
       }
     }
     if (__all_sync(0xffffffffu, mode == M_DONE)) break;
+    // ---- warp-uniform closest-node search for the lanes that start a candidate
+    {
+      const bool start = need && etype == E_INIT;
+      float xr[D];
+      if (start) rel_point<D>(*mp, e, xs, xr);
+      int nb = 0;
+      closest_node_warp<N, D, DR>(start, *mp, e, xs, xr, nb);
+      if (start) node_coords<N, DR>(B, nb, r);
+    }
     // ---- warp-uniform evaluation of x(r) and G(r) -------------------------
     if (need) {
       double re[DR];

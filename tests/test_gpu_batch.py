@@ -89,7 +89,7 @@ def test_batch_autotune_and_rerun(fp, torch, config4_small):
     first = [tuple(t.clone() for t in o[:4]) for o in b.outputs]
     b.autotune()
     infos = b.classes()
-    assert all(i.tuned_ms > 0 and i.ctas_per_sm in (2, 3, 4) and i.chunk_points in (32, 128, 512) for i in infos)
+    assert all(i.tuned_ms > 0 and 1 <= i.ctas_per_sm <= 4 and i.chunk_points in (32, 128, 512) for i in infos)
     for o in b.outputs:  # the autotuner overwrote the outputs: clear them
         o[0].fill_(7)
     b.run()
