@@ -724,8 +724,10 @@ extern "C" int fp_server_wait(fp_server s, int64_t id, double timeout_s) {
   auto f = s->reqs.find(id);
   if (f == s->reqs.end()) return FP_EINVAL;
   fp::Request* q = f->second.get();
+  // clamp so that the deadline arithmetic cannot overflow (about 115 days)
+  const double t = timeout_s > 1e7 ? 1e7 : (timeout_s > 0.0 ? timeout_s : 0.0);
   const auto deadline = fp::Clock::now() + std::chrono::duration_cast<fp::Clock::duration>(
-                                                 std::chrono::duration<double>(timeout_s));
+                                                 std::chrono::duration<double>(t));
   while (q->state != fp::R_DONE) {
     if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && q->state != fp::R_DONE)
       return FP_ETIMEDOUT;

@@ -24,7 +24,12 @@ def to_np(t):
     return t.detach().cpu().numpy()
 
 
-def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label="", xscale=1.0):
+def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label="", xscale=1.0, om=None, pts=None):
+    """om, pts (the oracle mesh and the points, optional): a BORDER point whose
+    closest point on the element is not unique to rounding (a point near a
+    centre of curvature of a surface or line, where the distance is almost
+    constant along the element) has many correct r; there the GPU's r is
+    accepted if the oracle's own map puts it at the oracle's distance."""
     oc, oe, orr, od = oracle_out
     gc, ge, gr, gd = gpu_out
     mism = (oc != gc) | (oe != ge)
@@ -36,8 +41,19 @@ def compare_find(oracle_out, gpu_out, r_tol=R_TOL, label="", xscale=1.0):
         f"{list(zip(oc[bad[:5]], oe[bad[:5]]))} gpu {list(zip(gc[bad[:5]], ge[bad[:5]]))}")
     same = ~mism & (oc != 2)
     if same.any():
-        dr = np.max(np.abs(orr[same] - gr[same]))
-        assert dr <= r_tol, f"{label}: max |dr| = {dr:.3e}"
+        drp = np.max(np.abs(orr - gr), axis=1)
+        off = same & (drp > r_tol)
+        if om is not None and np.any(off & (oc == 1)):
+            k = np.flatnonzero(off & (oc == 1))
+            x = om.forward_map(ge[k], gr[k])
+            d2 = np.sum((pts[k] - x) ** 2, axis=1)
+            tol = D2_REL * od[k] + D2_X * xscale * np.sqrt(od[k]) + D2_ABS
+            flat = np.zeros(len(oc), bool)
+            flat[k] = np.abs(d2 - od[k]) <= tol
+            off &= ~flat
+        dr = np.max(np.where(off, drp, 0.0))
+        assert not off.any(), (f"{label}: max |dr| = {dr:.3e} at {np.flatnonzero(off)[:5]}, codes "
+                               f"{oc[off][:5]}, dist2 {od[off][:5]}")
         tol = D2_REL * np.abs(od[same]) + D2_X * xscale * np.sqrt(np.abs(od[same])) + D2_ABS
         dd = np.abs(od[same] - gd[same]) - tol
         k = int(np.argmax(dd))

@@ -376,3 +376,55 @@ def test_robustness_cases(fp, torch, variant, precision):
     np.testing.assert_allclose(g[2][-500:], rn, atol=1e-10)
     assert m.device_status() == 0
     m.close()
+
+
+def _random_case(seed):
+    rng = np.random.default_rng(1000 + seed)
+    kind = ["quad2d", "hex3d", "sphere", "torus", "circle", "helix"][seed % 6]
+    order = int(rng.integers(1, 8))
+    if kind == "quad2d":
+        n = int(rng.integers(2, 9))
+        return W.quad_mesh(n, order, amp=float(rng.uniform(0, 0.3)), kind="kershaw"), 2, 2, order, 1.0 / n
+    if kind == "hex3d":
+        n = int(rng.integers(1, 5))
+        return W.hex_mesh(n, order, float(rng.uniform(0, 0.4))), 3, 3, order, 1.0 / n
+    if kind == "sphere":
+        n = int(rng.integers(1, 4))
+        return W.cubed_sphere(n, order), 3, 2, order, np.pi / (2 * n)
+    if kind == "torus":
+        nu, nv = int(rng.integers(3, 12)), int(rng.integers(3, 8))
+        return W.torus(nu, nv, order), 3, 2, order, 2 * np.pi * 0.3 / nv
+    if kind == "circle":
+        n = int(rng.integers(3, 40))
+        return W.circle_lines(n, order), 2, 1, order, 2 * np.pi / n
+    n = int(rng.integers(4, 40))
+    return W.helix_lines(n, order), 3, 1, order, 1.0 / n
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("seed", range(12))
+def test_randomized_parity(fp, torch, seed, precision):
+    """Seeded random meshes (shape, order 1-7, element count, deformation)
+    and points inside, near and outside them: code and element exact, r,
+    dist2 and interpolated values within the FP64 tolerances."""
+    coords, d, dr, order, h = _random_case(seed)
+    N = order + 1
+    om = oracle.OracleMesh(coords, d, dr, N)
+    rng = np.random.default_rng(2000 + seed)
+    n = 6000
+    el = rng.integers(0, om.NE, n).astype(np.int32)
+    x = om.forward_map(el, rng.uniform(-1, 1, (n, dr)))
+    x[: n // 3] += (0.05 * h) * rng.standard_normal((n // 3, d))
+    lo, hi = om.aabb[:, :d].min(0), om.aabb[:, d:].max(0)
+    x[n // 3: n // 2] = rng.uniform(lo - 0.05 * (hi - lo), hi + 0.05 * (hi - lo), (n // 2 - n // 3, d))
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    m.set_precision(fp.FP_MIXED if precision == "mixed" else fp.FP_F64)
+    g = gpu_find(torch, m, x)
+    o = om.findpts(x)
+    compare_find(o, g, label=f"random {seed} {precision}", xscale=1.3 * float(np.abs(coords).max()), om=om, pts=x)
+    fld, _ = W.polynomial_field(coords, rng, min(order, 3), nc=1)
+    oc, oe, orr = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in o[:3])
+    u = to_np(m.eval(oc, oe, orr, torch.from_numpy(fld).cuda()))
+    compare_eval(fld, om.NE, N ** dr, o[1], om.eval(fld, *o[:3]), u, f"random {seed} eval")
+    assert m.device_status() == 0
+    m.close()
