@@ -75,10 +75,13 @@ extern "C" {
  * counting sort on the device, for calls of at least 16384 points), so the
  * points a warp handles share candidate elements; the paper's remark on the
  * CPU implementation (Sec. 3.2) that processing the points of an element
- * together improves locality.  FP_ORDER_GIVEN takes the points as given.
- * The outputs are identical either way; only the speed differs.  The cell
- * order needs 8 bytes per point plus 8 bytes per cell of scratch, taken from
- * the stream-ordered allocator for the duration of the call. */
+ * together improves locality.  The cells' points come in four cost classes
+ * (3 or more candidate boxes, 2, 1, none), the costly ones first, so the end
+ * of a launch, where lanes wait for the slowest point of their warp, runs
+ * cheap points.  FP_ORDER_GIVEN takes the points as given.  The outputs are
+ * identical either way; only the speed differs.  The cell order needs 8
+ * bytes per point plus 32 bytes per cell of scratch, taken from the
+ * stream-ordered allocator for the duration of the call. */
 #define FP_ORDER_GIVEN 0
 #define FP_ORDER_CELL 1
 
@@ -172,6 +175,25 @@ int fp_findpts_mixed_noalloc(fp_mesh m, const double* pts_dev, int64_t n, int32_
  * serves any number of fields.  Errors: FP_EINVAL, FP_ELAUNCH. */
 int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
             int64_t n, const double* field_dev, int nc, double* out, void* stream);
+
+/* Find, and optionally Interpolate, end to end from host memory.  The paper
+ * has no counterpart: it is fp_findpts followed by fp_eval, with the points
+ * copied to the device and the results copied back in chunks of `chunk`
+ * points (0: automatic, four chunks of at least 2^21 points), each chunk's
+ * copies overlapping the search of the others, and consecutive chunks
+ * searched on two streams so that one's launch fills the other's tail.
+ *   pts_host [n][d]; outputs code_host [n], elem_host [n], r_host [n][dr],
+ *   dist2_host [n] as fp_findpts; with field_dev (device, [nc][NE][N^dr])
+ *   not NULL, out_host [nc][n] as fp_eval.  All host buffers should be
+ *   pinned (page-locked), or the copies do not overlap the kernels.
+ * Device scratch: (8 (d + dr + 1 + nc) + 8) bytes per point, plus the cell
+ * order's, from the stream-ordered allocator for the duration of the call.
+ * Synchronous: returns when the results are in host memory.
+ * Errors: FP_EINVAL, FP_ENOMEM, FP_ELAUNCH. */
+int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int32_t* code_host,
+                    int32_t* elem_host, double* r_host, double* dist2_host,
+                    const double* field_dev, int nc, double* out_host, int64_t chunk,
+                    void* stream);
 
 /* Interpolate a field of another order (Sec. 2, after Eq. u_tensor: the
  * solution's order N~ - 1 often differs from the coordinates' order N - 1).

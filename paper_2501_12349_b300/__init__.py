@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
             "fp_findpts_stats": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fp_eval": ([_vp, _vp, _vp, _vp, _i64, _vp, _int, _vp, _vp], _int),
             "fp_eval_order": ([_vp, _vp, _vp, _vp, _i64, _vp, _int, _int, _vp, _vp], _int),
+            "fp_findpts_host": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _int, _vp, _i64, _vp], _int),
             "fp_get_info": ([_vp, ctypes.POINTER(FpMeshInfo)], _int),
             "fp_get_boxes": ([_vp, _vp, _vp, _vp, _vp], _int),
             "fp_get_grid": ([_vp, _vp, _vp, _vp], _int),
@@ -176,6 +177,25 @@ def fp_eval_order(mesh, code, elem, r, field, field_order: int, nc: int, out, st
         mesh, _ptr(code, torch.int32, "code"), _ptr(elem, torch.int32, "elem"),
         _ptr(r, torch.float64, "r"), n, _ptr(field, torch.float64, "field"), int(field_order), int(nc),
         _ptr(out, torch.float64, "out"), _stream(stream)))
+
+
+def fp_findpts_host(mesh, pts, code, elem, r, dist2, field=None, nc: int = 0, out=None, chunk: int = 0,
+                    stream=None) -> None:
+    """Host tensors (pinned CPU torch tensors for overlapped copies): pts
+    [n][d] float64; outputs code, elem int32 [n], r [n][dr], dist2 [n]; field
+    a device tensor [nc][NE][N^dr] or None, out [nc][n] host."""
+    import torch
+
+    def hp(t, dt, name):
+        if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous CPU {dt} tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    n = pts.shape[0]
+    _check("fp_findpts_host", lib().fp_findpts_host(
+        mesh, hp(pts, torch.float64, "pts"), n, hp(code, torch.int32, "code"), hp(elem, torch.int32, "elem"),
+        hp(r, torch.float64, "r"), hp(dist2, torch.float64, "dist2"),
+        None if field is None else _ptr(field, torch.float64, "field"), int(nc) if field is not None else 0,
+        None if field is None else hp(out, torch.float64, "out"), int(chunk), _stream(stream)))
 
 
 def fp_get_info(mesh) -> FpMeshInfo:
@@ -525,6 +545,22 @@ class Mesh:
         else:
             fp_eval_order(self.handle, code, elem, r, field, order, nc, out, stream)
         return out
+
+    def find_host(self, pts, field=None, chunk: int = 0, stream=None):
+        """fp_findpts_host: pts a CPU float64 tensor [n][d] (pinned for
+        overlapped copies); returns pinned CPU tensors (code, elem, r, dist2)
+        and, with a device field [nc][NE][N^dr], the values [nc][n]."""
+        import torch
+        n = pts.shape[0]
+        pin = pts.is_pinned()
+        code = torch.empty(n, dtype=torch.int32, pin_memory=pin)
+        elem = torch.empty(n, dtype=torch.int32, pin_memory=pin)
+        r = torch.empty((n, self.dr), dtype=torch.float64, pin_memory=pin)
+        dist2 = torch.empty(n, dtype=torch.float64, pin_memory=pin)
+        nc = 0 if field is None else field.numel() // (self.NE * self.N ** self.dr)
+        out = None if field is None else torch.empty((nc, n), dtype=torch.float64, pin_memory=pin)
+        fp_findpts_host(self.handle, pts, code, elem, r, dist2, field, nc, out, chunk, stream)
+        return (code, elem, r, dist2) if field is None else (code, elem, r, dist2, out)
 
     def info(self) -> FpMeshInfo:
         return fp_get_info(self.handle)

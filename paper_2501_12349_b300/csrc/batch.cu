@@ -272,8 +272,8 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
       break;
     }
     // the cell order (as for single-mesh calls of at least 16384 points)
-    if (!c.unordered && c.total >= (1 << 14) && c.buckets + 1 < INT32_MAX &&
-        cudaMalloc(&c.d_order, sizeof(int) * (size_t)(2 * c.total + 2 * c.buckets + 1)) != cudaSuccess) {
+    if (!c.unordered && c.total >= (1 << 14) && 4 * c.buckets + 1 < INT32_MAX &&
+        cudaMalloc(&c.d_order, sizeof(int) * (size_t)batch_cell_order_ints(c.total, c.buckets)) != cudaSuccess) {
       rc = FP_ENOMEM;
       break;
     }

@@ -637,8 +637,10 @@ int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N,
 int64_t cell_order_ints(const fp_mesh_s* m, int64_t n);
 int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, int** perm, cudaStream_t st);
 // The same for one element shape of a batch: the points of all items grouped
-// by (item, Psi_L cell); buckets = sum over items of (cells + 1), with each
-// item's cell_base set; scratch of 2 total + 2 buckets + 1 ints.
+// by cost class, then (item, Psi_L cell); buckets = sum over items of
+// (cells + 1), with each item's cell_base set; scratch of
+// batch_cell_order_ints(total, buckets) ints.
+int64_t batch_cell_order_ints(int64_t total, int64_t buckets);
 int batch_cell_order(const BatchItem* items, int nitems, int64_t total, int d, int64_t buckets, int* scratch,
                      int** perm, cudaStream_t st);
 

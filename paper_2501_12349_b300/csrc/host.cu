@@ -1,0 +1,109 @@
+// fp_findpts_host: Find (and Interpolate) end to end from host memory, with
+// the host<->device copies of one chunk of points overlapping the search of
+// another.
+//
+// Chunk k's points go to the device on a copy stream; a compute stream (the
+// caller's for even k, a second one for odd k) waits for them, searches the
+// chunk (fp_findpts, with its cell order) and interpolates the field
+// (fp_eval); the copy stream then waits for that and brings the chunk's
+// results back while the next chunk is searched.  Only the first upload and
+// the last download are not hidden behind kernels.  Two compute streams let
+// the next chunk's persistent find launch take the SMs that the current one
+// leaves during its tail (its last points run with few lanes), which a
+// single stream would leave idle.
+#include <stdlib.h>
+
+#include <vector>
+
+#include "fp_common.cuh"
+
+namespace {
+
+// Each chunk costs the tail of its find launch (about half a millisecond at
+// 10^6 points) and saves the copy time of a chunk (about a millisecond per
+// 10^6 points in and out), so chunking pays only for large calls: four
+// chunks, at least 2^21 points each (one chunk below 2^22 points).
+int64_t auto_chunk(int64_t n) {
+  const int64_t c = (n + 3) / 4;
+  return c < ((int64_t)1 << 21) ? ((int64_t)1 << 21) : c;
+}
+
+}  // namespace
+
+extern "C" int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int32_t* code_host,
+                               int32_t* elem_host, double* r_host, double* dist2_host,
+                               const double* field_dev, int nc, double* out_host, int64_t chunk,
+                               void* stream) {
+  if (!m || n < 0 || n > INT32_MAX || chunk < 0) return FP_EINVAL;
+  if (n == 0) return FP_OK;
+  if (!pts_host || !code_host || !elem_host || !r_host || !dist2_host) return FP_EINVAL;
+  if (field_dev && (nc <= 0 || !out_host)) return FP_EINVAL;
+  if (!field_dev) nc = 0;
+  const int d = m->d, dr = m->dr;
+  const int64_t C = chunk > 0 ? (chunk < n ? chunk : n) : (auto_chunk(n) < n ? auto_chunk(n) : n);
+  const int64_t K = (n + C - 1) / C;
+  cudaStream_t st = (cudaStream_t)stream;
+  // device buffers, in doubles: points, r, dist2, values; then code, elem
+  const size_t nd = (size_t)n * (d + dr + 1) + (size_t)nc * n;
+  const size_t bytes = nd * sizeof(double) + 2 * (size_t)n * sizeof(int32_t);
+  char* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, bytes, st) != cudaSuccess) return FP_ENOMEM;
+  double* pts = (double*)buf;
+  double* r = pts + (size_t)n * d;
+  double* dist2 = r + (size_t)n * dr;
+  double* out = dist2 + n;  // [K][nc][C]: each chunk's values together
+  int32_t* code = (int32_t*)(out + (size_t)nc * n);
+  int32_t* elem = code + n;
+  cudaStream_t cp = nullptr, c1 = nullptr;
+  std::vector<cudaEvent_t> ev(2 * K + 2, nullptr);
+  int rc = FP_OK;
+  if (cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c1, cudaStreamNonBlocking) != cudaSuccess)
+    rc = FP_ELAUNCH;
+  for (auto& e : ev)
+    if (rc == FP_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = FP_ELAUNCH;
+  // the other streams start after the allocation on the caller's stream
+  if (rc == FP_OK && (cudaEventRecord(ev[2 * K], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev[2 * K], 0) != cudaSuccess ||
+                      cudaStreamWaitEvent(c1, ev[2 * K], 0) != cudaSuccess))
+    rc = FP_ELAUNCH;
+  for (int64_t k = 0; k < K && rc == FP_OK; ++k) {
+    const int64_t off = k * C, len = (n - off < C) ? n - off : C;
+    cudaStream_t cs = (k % 2 == 0) ? st : c1;
+    if (cudaMemcpyAsync(pts + off * d, pts_host + off * d, sizeof(double) * len * d, cudaMemcpyHostToDevice,
+                        cp) != cudaSuccess ||
+        cudaEventRecord(ev[2 * k], cp) != cudaSuccess || cudaStreamWaitEvent(cs, ev[2 * k], 0) != cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+    rc = fp_findpts(m, pts + off * d, len, code + off, elem + off, r + off * dr, dist2 + off, cs);
+    double* o = out + (size_t)nc * off;
+    if (rc == FP_OK && nc > 0) rc = fp_eval(m, code + off, elem + off, r + off * dr, len, field_dev, nc, o, cs);
+    if (rc != FP_OK) break;
+    if (cudaEventRecord(ev[2 * k + 1], cs) != cudaSuccess || cudaStreamWaitEvent(cp, ev[2 * k + 1], 0) != cudaSuccess) {
+      rc = FP_ELAUNCH;
+      break;
+    }
+    cudaError_t e = cudaMemcpyAsync(code_host + off, code + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, cp);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(elem_host + off, elem + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, cp);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r_host + off * dr, r + off * dr, sizeof(double) * len * dr, cudaMemcpyDeviceToHost, cp);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dist2_host + off, dist2 + off, sizeof(double) * len, cudaMemcpyDeviceToHost, cp);
+    if (e == cudaSuccess && nc > 0)  // [nc][len] on the device into rows of [nc][n]
+      e = cudaMemcpy2DAsync(out_host + off, sizeof(double) * n, o, sizeof(double) * len, sizeof(double) * len, nc,
+                            cudaMemcpyDeviceToHost, cp);
+    if (e != cudaSuccess) rc = FP_ELAUNCH;
+  }
+  // whatever happened, the buffer is freed after every copy and kernel
+  if (c1 && cudaEventRecord(ev[2 * K + 1], c1) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K + 1], 0);
+  if (cp && cudaEventRecord(ev[2 * K], cp) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K], 0);
+  cudaFreeAsync(buf, st);
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (rc == FP_OK && es != cudaSuccess) rc = FP_ELAUNCH;
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (cp) cudaStreamDestroy(cp);
+  if (c1) cudaStreamDestroy(c1);
+  return rc;
+}

@@ -21,16 +21,37 @@ namespace fp {
 
 namespace {
 
+constexpr int kCostClasses = 4;  // candidates 3+, 2, 1, 0
+
+// Bucket of a point: its cost class, then its cell.  The class counts the
+// candidate elements whose boxes may hold the point (the FP32 box test,
+// undecided cases counted), 3 or more first: every candidate but the last
+// costs a Newton run, so points with many candidates are the slow ones, and
+// taking them first leaves cheap points for the end of the launch, where
+// lanes that run out of points wait for the slowest of their warp.
 template <int D>
 __global__ void __launch_bounds__(256)
     k_point_cells(const __grid_constant__ DevMesh m, int64_t ncell, const double* __restrict__ pts, int64_t n,
                   int* __restrict__ cellof, int* __restrict__ counts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double xs[D];
+    float x32[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) xs[c] = __ldg(pts + i * D + c);
+    for (int c = 0; c < D; ++c) {
+      xs[c] = __ldg(pts + i * D + c);
+      x32[c] = (float)xs[c];
+    }
     const int64_t cell = point_cell<D>(m, xs);
-    const int k = cell < 0 ? (int)ncell : (int)cell;
+    int k;
+    if (cell < 0) {
+      k = (int)(kCostClasses * (ncell + 1) - 1);
+    } else {
+      int cand = 0;
+      const int q0 = __ldg(m.cell_start + cell), q1 = __ldg(m.cell_start + cell + 1);
+      for (int q = q0; q < q1 && cand < kCostClasses - 1; ++q)
+        cand += boxes_f32<D>(m.box32 + (int64_t)__ldg(m.cell_elems + q) * BOX32, x32) != 0;
+      k = (int)((kCostClasses - 1 - cand) * (ncell + 1) + cell);
+    }
     cellof[i] = k;
     atomicAdd(counts + k, 1);
   }
@@ -47,8 +68,8 @@ __global__ void __launch_bounds__(256)
 
 template <int D>
 __global__ void __launch_bounds__(256)
-    k_batch_point_cells(const BatchItem* __restrict__ items, int nitems, int64_t total, int* __restrict__ key,
-                        int* __restrict__ counts) {
+    k_batch_point_cells(const BatchItem* __restrict__ items, int nitems, int64_t total, int64_t buckets,
+                        int* __restrict__ key, int* __restrict__ counts) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
     int lo = 0, hi = nitems - 1;
@@ -60,48 +81,125 @@ __global__ void __launch_bounds__(256)
     const BatchItem& it = items[lo];
     const int64_t p = g - it.start;
     double xs[D];
+    float x32[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) xs[c] = __ldg(it.pts + p * D + c);
+    for (int c = 0; c < D; ++c) {
+      xs[c] = __ldg(it.pts + p * D + c);
+      x32[c] = (float)xs[c];
+    }
     int64_t ncell = 1;
 #pragma unroll
     for (int c = 0; c < D; ++c) ncell *= it.m.NL;
     const int64_t cell = point_cell<D>(it.m, xs);
-    const int k = (int)(it.cell_base + (cell < 0 ? ncell : cell));
+    int cand = 0;
+    if (cell >= 0) {  // the cost class, as in k_point_cells
+      const int q0 = __ldg(it.m.cell_start + cell), q1 = __ldg(it.m.cell_start + cell + 1);
+      for (int q = q0; q < q1 && cand < kCostClasses - 1; ++q)
+        cand += boxes_f32<D>(it.m.box32 + (int64_t)__ldg(it.m.cell_elems + q) * BOX32, x32) != 0;
+    }
+    const int k = (int)((kCostClasses - 1 - cand) * buckets + it.cell_base + (cell < 0 ? ncell : cell));
     key[g] = k;
     atomicAdd(counts + k, 1);
   }
 }
 
+// Exclusive scan of counts[0, n) into start[0, n], start[n] = total, over
+// tiles of kScanTile elements: each CTA scans its tile and writes the tile's
+// total; one CTA scans the tile totals; a last pass adds each tile's offset.
+constexpr int kScanThreads = 512, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_tiles(const int* __restrict__ counts, int64_t n, int* __restrict__ start, int* __restrict__ tile_sum) {
+  __shared__ int s[kScanThreads];
+  const int t = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)t * kScanItems;
+  int v[kScanItems], sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < n ? counts[base + k] : 0;
+    sum += v[k];
+  }
+  s[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {
+    const int add = t >= o ? s[t - o] : 0;
+    __syncthreads();
+    s[t] += add;
+    __syncthreads();
+  }
+  int run = s[t] - sum;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) start[base + k] = run;
+    run += v[k];
+  }
+  if (t == kScanThreads - 1) tile_sum[blockIdx.x] = s[t];
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_add(int* __restrict__ start, int64_t n, const int* __restrict__ tile_pre, int64_t ntiles) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  const int off = tile_pre[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads)
+    if (base + k < n) start[base + k] += off;
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[n] = tile_pre[ntiles];
+}
+
+int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+// scratch: 2 scan_tiles(n) + 1 ints
+int exclusive_scan(const int* counts, int64_t n, int* start, int* scratch, cudaStream_t st) {
+  const int64_t nt = scan_tiles(n);
+  int* tsum = scratch;
+  int* tpre = scratch + nt;
+  k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, st>>>(counts, n, start, tsum);
+  k_scan<<<1, 1024, 0, st>>>(tsum, nt, tpre);
+  k_scan_add<<<(unsigned)nt, kScanThreads, 0, st>>>(start, n, tpre, nt);
+  FP_CUDA_TRY(cudaGetLastError());
+  return FP_OK;
+}
+
 }  // namespace
+
+int64_t batch_cell_order_ints(int64_t total, int64_t buckets) {
+  const int64_t nb = kCostClasses * buckets;
+  return 2 * total + 2 * nb + 1 + 2 * scan_tiles(nb) + 1;
+}
 
 int batch_cell_order(const BatchItem* items, int nitems, int64_t total, int d, int64_t buckets, int* scratch,
                      int** perm, cudaStream_t st) {
-  int* p = scratch;               // [total]
-  int* key = p + total;           // [total]
-  int* counts = key + total;      // [buckets]
-  int* start = counts + buckets;  // [buckets + 1]
-  FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)buckets, st));
+  const int64_t nb = kCostClasses * buckets;  // cost class x (items' cells)
+  int* p = scratch;          // [total]
+  int* key = p + total;      // [total]
+  int* counts = key + total; // [nb]
+  int* start = counts + nb;  // [nb + 1]
+  int* sc = start + nb + 1;  // scan scratch
+  FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)nb, st));
   const int blocks = (int)((total + 255) / 256 < 8 * 148 ? (total + 255) / 256 : 8 * 148);
   if (d == 2)
-    k_batch_point_cells<2><<<blocks, 256, 0, st>>>(items, nitems, total, key, counts);
+    k_batch_point_cells<2><<<blocks, 256, 0, st>>>(items, nitems, total, buckets, key, counts);
   else
-    k_batch_point_cells<3><<<blocks, 256, 0, st>>>(items, nitems, total, key, counts);
-  k_scan<<<1, 1024, 0, st>>>(counts, buckets, start);
-  FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)buckets, st));
+    k_batch_point_cells<3><<<blocks, 256, 0, st>>>(items, nitems, total, buckets, key, counts);
+  FP_TRY(exclusive_scan(counts, nb, start, sc, st));
+  FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)nb, st));
   k_point_scatter<<<blocks, 256, 0, st>>>(key, total, start, counts, p);
   FP_CUDA_TRY(cudaGetLastError());
   *perm = p;
   return FP_OK;
 }
 
-int64_t cell_order_ints(const fp_mesh_s* m, int64_t n) { return 2 * n + 2 * (m->ncell + 1) + 1; }
+int64_t cell_order_ints(const fp_mesh_s* m, int64_t n) {
+  const int64_t nb = kCostClasses * (m->ncell + 1);
+  return 2 * n + 2 * nb + 1 + 2 * scan_tiles(nb) + 1;
+}
 
 int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, int** perm, cudaStream_t st) {
-  const int64_t nb = m->ncell + 1;  // buckets: the cells and "outside"
+  const int64_t nb = kCostClasses * (m->ncell + 1);  // buckets: cost class x (cells and "outside")
   int* p = scratch;                  // [n]
   int* cellof = p + n;               // [n]
   int* counts = cellof + n;          // [nb], reused as the scatter cursors
   int* start = counts + nb;          // [nb + 1]
+  int* sc = start + nb + 1;          // scan scratch
   FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)nb, st));
   const DevMesh v = m->view();
   const int blocks = (int)((n + 255) / 256 < 8 * 148 ? (n + 255) / 256 : 8 * 148);
@@ -109,7 +207,7 @@ int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, i
     k_point_cells<2><<<blocks, 256, 0, st>>>(v, m->ncell, pts, n, cellof, counts);
   else
     k_point_cells<3><<<blocks, 256, 0, st>>>(v, m->ncell, pts, n, cellof, counts);
-  k_scan<<<1, 1024, 0, st>>>(counts, nb, start);
+  FP_TRY(exclusive_scan(counts, nb, start, sc, st));
   FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)nb, st));
   k_point_scatter<<<blocks, 256, 0, st>>>(cellof, n, start, counts, p);
   FP_CUDA_TRY(cudaGetLastError());

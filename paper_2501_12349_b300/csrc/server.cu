@@ -467,7 +467,7 @@ int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& lau
     if (s->opts.precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qq + total, 0, sizeof(int), t.st));
     // the shapes run one after another on t.st, so they share the scratch
     int* order = nullptr;
-    if (total >= (1 << 14) && 2 * total + 2 * buckets + 1 <= t.order_cap)
+    if (total >= (1 << 14) && batch_cell_order_ints(total, buckets) <= t.order_cap)
       FP_TRY(batch_cell_order(t.items_d + first, cnt, total, d, buckets, t.order, &order, t.st));
     FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision,
                               0, 5, order, qq, qq + total, nullptr, t.st));
@@ -642,7 +642,7 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
   const int64_t qcap = (int64_t)(o.mem_budget / 72) + 2 * 64 + 16;
   int64_t all_buckets = 0;
   for (auto& me : s->meshes) all_buckets += me.m->ncell + 1;
-  const int64_t ocap = 2 * std::min(qcap, o.tick_points) + 2 * all_buckets + 1;
+  const int64_t ocap = batch_cell_order_ints(std::min(qcap, o.tick_points), all_buckets);
   int rc = FP_OK;
   if (!s->arena.init(o.mem_budget)) rc = FP_ENOMEM;
   if (rc == FP_OK && cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess) rc = FP_ELAUNCH;

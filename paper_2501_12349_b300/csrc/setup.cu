@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "fp_basis.cuh"
@@ -811,10 +812,35 @@ extern "C" void fp_opts_default(fp_opts* o) {
   o->point_order = FP_ORDER_CELL;
 }
 
+namespace {
+
+// Find calls take their scratch (the cell order, the mixed path's queue,
+// the host path's buffers) from the device's default stream-ordered pool;
+// by default the pool hands freed memory back at every synchronisation, so
+// each call would pay a fresh allocation.  Keeping up to 1 GiB of freed
+// scratch in the pool (per process, per device) lets calls reuse it.
+void keep_pool_memory() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = (uint64_t)1 << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
+}
+
+}  // namespace
+
 extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int64_t NE,
                         const fp_opts* opts, void* stream, fp_mesh* out) {
   using namespace fp;
   if (!out) return FP_EINVAL;
+  keep_pool_memory();
   *out = nullptr;
   if (!coords_dev || NE <= 0 || NE > INT32_MAX) return FP_EINVAL;
   if (!((d == 2 && dr == 2) || (d == 3 && dr == 3) || (d == 3 && dr == 2) || (dr == 1 && (d == 2 || d == 3))))

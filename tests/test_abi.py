@@ -55,6 +55,7 @@ def test_argument_checks_without_device(lib):
     assert lib.fp_free(None) == fp.FP_EINVAL
     assert lib.fp_set_precision(None, 0) == fp.FP_EINVAL
     assert lib.fp_set_point_order(None, fp.FP_ORDER_CELL) == fp.FP_EINVAL
+    assert lib.fp_findpts_host(None, None, 10, None, None, None, None, None, 0, None, 0, None) == fp.FP_EINVAL
 
 
 def test_header_constants_match_binding():

@@ -428,3 +428,26 @@ def test_randomized_parity(fp, torch, seed, precision):
     compare_eval(fld, om.NE, N ** dr, o[1], om.eval(fld, *o[:3]), u, f"random {seed} eval")
     assert m.device_status() == 0
     m.close()
+
+
+@pytest.mark.parametrize("chunk", [0, 1000, 7919, 10 ** 9])
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_findpts_host(fp, torch, chunk, precision):
+    """fp_findpts_host (host buffers, chunked copies overlapping the search)
+    gives the device path's outputs bit for bit, with and without a field."""
+    coords, d, dr, order, h = CASES["hex3d_p4"]()
+    rng = np.random.default_rng(17)
+    pts = rng.uniform(-0.05, 1.05, (30000, 3))
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    m.set_precision(fp.FP_MIXED if precision == "mixed" else fp.FP_F64)
+    fld = torch.from_numpy(rng.uniform(-1, 1, (2, m.NE * (order + 1) ** 3))).cuda()
+    ref = m.find(torch.from_numpy(pts).cuda())
+    uref = m.eval(*ref[:3], fld)
+    hp = torch.from_numpy(pts).pin_memory()
+    got = m.find_host(hp, fld, chunk=chunk)
+    for a, b in zip(list(ref) + [uref], got):
+        assert torch.equal(a.cpu(), b)
+    got2 = m.find_host(hp, None, chunk=chunk)
+    for a, b in zip(ref, got2):
+        assert torch.equal(a.cpu(), b)
+    m.close()
