@@ -62,10 +62,10 @@ __device__ __forceinline__ BetaReq beta_request(bool want, const T (&r)[DR], con
     T g = T(0);
 #pragma unroll
     for (int c = 0; c < D; ++c) g -= G[c * DR + j] * dx[c];
-    const bool onb = (r[j] == T(-1) || r[j] == T(1));
-    const bool held = (r[j] == T(-1) && g > T(0)) || (r[j] == T(1) && g < T(0));
+    const bool onb = is_unit(r[j]);
+    const bool held = held_at_bound(r[j], g);
     full |= onb && !held;
-    if (held) base += (r[j] == T(1) ? N - 1 : 0) * stride[j];
+    if (held) base += (sign_bit(r[j]) ? 0 : N - 1) * stride[j];
     else fr[nf++] = j;
   }
   if (full) {

@@ -352,11 +352,31 @@ __device__ __forceinline__ void write_result(int64_t p, int code_, int e, const 
 
 // ---- the trust-region step of Sec. 3.2.1 ------------------------------------
 
+// |v| == 1, |v| < 1 and the sign of v from the bit pattern, on the integer
+// pipe (the FP64 one is the kernels' bound): exact for every value, NaN
+// included (neither test holds for it), -0 included (|-0| < 1).
+__device__ __forceinline__ bool is_unit(double v) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) == 0x3ff0000000000000LL;
+}
+__device__ __forceinline__ bool is_unit(float v) { return (__float_as_int(v) & 0x7fffffff) == 0x3f800000; }
+__device__ __forceinline__ bool below_unit(double v) {
+  return (__double_as_longlong(v) & 0x7fffffffffffffffLL) < 0x3ff0000000000000LL;
+}
+__device__ __forceinline__ bool below_unit(float v) { return (__float_as_int(v) & 0x7fffffff) < 0x3f800000; }
+__device__ __forceinline__ bool sign_bit(double v) { return __double_as_longlong(v) < 0; }
+__device__ __forceinline__ bool sign_bit(float v) { return __float_as_int(v) < 0; }
+
+// r_j = -1 with the gradient pointing out (g > 0), or r_j = +1 with g < 0.
+template <typename T>
+__device__ __forceinline__ bool held_at_bound(T r, T g) {
+  return is_unit(r) && (sign_bit(r) ? g > T(0) : g < T(0));
+}
+
 template <int DR, typename T>
 __device__ __forceinline__ bool at_bound(const T (&r)[DR]) {
   bool b = false;
 #pragma unroll
-  for (int j = 0; j < DR; ++j) b |= (r[j] == T(-1) || r[j] == T(1));
+  for (int j = 0; j < DR; ++j) b |= is_unit(r[j]);
   return b;
 }
 
@@ -440,7 +460,7 @@ __device__ __forceinline__ T newton_step(const T (&G)[D * DR], const T (&dx)[D],
 #pragma unroll
     for (int c = 0; c < D; ++c) s -= G[c * DR + j] * dx[c];
     g[j] = s;
-    held[j] = (r[j] == T(-1) && s > T(0)) || (r[j] == T(1) && s < T(0));
+    held[j] = held_at_bound(r[j], s);
   }
 #pragma unroll
   for (int j = 0; j < DR; ++j)

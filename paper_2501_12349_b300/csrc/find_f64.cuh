@@ -145,7 +145,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
       if (done) {
         bool inside = true;
 #pragma unroll
-        for (int j = 0; j < DR; ++j) inside &= fabs(r[j]) < 1.0;
+        for (int j = 0; j < DR; ++j) inside &= below_unit(r[j]);
         if (DR < D) inside &= F < mp->dist_tol;
         if (inside || F < bd) {
           bcode = inside ? FP_INTERIOR : FP_BORDER;

@@ -180,7 +180,7 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
       if (done) {
         bool inside = true;
 #pragma unroll
-        for (int j = 0; j < DR; ++j) inside &= fabsf(r[j]) < 1.f;
+        for (int j = 0; j < DR; ++j) inside &= below_unit(r[j]);
         const float far2 = (kBorder32 * xrel) * (kBorder32 * xrel);
         const float dtol = (float)mp->dist_tol;
         if (converged && inside && (DR == D || F < 0.5f * dtol)) {
@@ -256,7 +256,7 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
 #pragma unroll
       for (int j = 0; j < DR; ++j) {
         rnn[j] = r64[j] + s[j];
-        inside &= fabs(rnn[j]) < 1.0;
+        inside &= below_unit(rnn[j]);
         mx = fmax(mx, fabs(s[j]));
       }
       if (!inside) {
