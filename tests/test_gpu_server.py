@@ -195,3 +195,28 @@ def test_tiles_small_ticks(fp, torch, resident):
     s.wait(big, timeout_s=120)
     assert s.stats().ticks > 60
     s.close()
+
+
+def test_tick_watchdog(fp, torch, resident):
+    """A tick past the watchdog limit fails its requests with FP_ETIMEDOUT on
+    the host (the kernels themselves finish normally; no GPU fault is
+    involved), the request memory is released once the tick has ended, and
+    the server keeps serving with a normal limit afterwards."""
+    import time
+    s = server_of(fp, resident, tick_timeout_s=1e-7)
+    rng = np.random.default_rng(57)
+    rid = s.submit(0, fp.FP_REQ_PARTICLE, rng.uniform(0.05, 0.95, (200000, 3)), rk_steps=2, dt=0.001)
+    with pytest.raises(fp.FindptsError) as err:
+        s.wait(rid, timeout_s=60)
+    assert err.value.status == fp.FP_ETIMEDOUT
+    st = s.stats()
+    assert st.timeouts >= 1
+    deadline = time.time() + 30
+    while s.stats().bytes_in_use != 0 and time.time() < deadline:
+        time.sleep(0.01)
+    assert s.stats().bytes_in_use == 0 and s.stats().active == 0
+    s.close()
+    s2 = server_of(fp, resident)
+    code, elem, r, d2, u = s2.wait(s2.submit(0, fp.FP_REQ_REMAP, rng.uniform(0, 1, (1000, 3))))
+    assert np.all(code != 2)
+    s2.close()
