@@ -40,7 +40,7 @@ WORKLOAD = "hex3d_32^3_p4_kershaw0.3_1e6pts"
 # DRAM bytes (read + write) of one k_find_f64 launch on the 32^3 p=4 mesh with
 # 10^6 points, from one ncu capture of the current kernel (the summary under
 # profiles/ gives the command); None once the kernel changes.
-F64_TRAFFIC = None
+F64_TRAFFIC = 853.5e6
 
 
 def flop_terms(N, d, dr):
@@ -84,13 +84,19 @@ def flop_model(stats, N, d, dr, n_found, nc):
 def mixed_flop_model(stats, N, d, dr):
     """(FP32, FP64) algorithmic flops of one mixed-precision find: the FP32
     kernel's candidates, steps and evaluations (linearised initial guess
-    instead of the node search), its FP64 refinements (x(r) in d
-    components, residual, normal equations, solve), and the FP64 kernel on
-    the handed-over points (counters [8]-[15])."""
+    instead of the node search), its refinements (x(r) in d components and
+    the residual in FP64; the normal equations and their solve in FP32 for
+    volumes, in FP64 with the FP64 Jacobian for surfaces and lines), and the
+    FP64 kernel on the handed-over points (counters [8]-[15])."""
     t = flop_terms(N, d, dr)
     C, R = int(stats[0]), int(stats[4])
     f32 = C * 2 * d * dr + find_flops(stats[0:8], N, d, dr, node=False)
-    refine = d * (t["eval_x"] - t["basis"]) + t["basis"] + 2 * d + 2 * d * dr * (dr + 1) + 30
+    refine = d * (t["eval_x"] - t["basis"]) + t["basis"] + 2 * d
+    solve = 2 * d * dr * (dr + 1) + 30
+    if dr == d:
+        f32 += R * solve
+    else:
+        refine += solve
     f64 = R * refine + find_flops(stats[8:16], N, d, dr, node=False)
     return float(f32), float(f64)
 

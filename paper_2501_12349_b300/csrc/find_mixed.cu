@@ -43,6 +43,41 @@ constexpr int kMaxRefine = 4;
 // half of the statistics array, so the two precisions' work stays separate.
 inline unsigned long long* fallback_stats(unsigned long long* stats) { return stats ? stats + 8 : nullptr; }
 
+// Gauss-Newton correction s from (G^T G) s = G^T dx, in the precision T of
+// its arguments; false where G^T G is not positive definite or det(G^T G) is
+// below rel_det times the product of its diagonal (ill-conditioned for T).
+template <int D, int DR, typename T>
+__device__ __forceinline__ bool gauss_newton_step(const T* G, const T (&dx)[D], T rel_det, T (&s)[DR]) {
+  T H[DR][DR], b[DR];
+#pragma unroll
+  for (int j = 0; j < DR; ++j) {
+    T t = T(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) t += G[c * DR + j] * dx[c];
+    b[j] = t;
+#pragma unroll
+    for (int k = 0; k < DR; ++k) {
+      T u = T(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) u += G[c * DR + j] * G[c * DR + k];
+      H[j][k] = u;
+    }
+  }
+  T dprod = T(1);
+#pragma unroll
+  for (int j = 0; j < DR; ++j) dprod *= H[j][j];
+  T det;
+  if constexpr (DR == 1) {
+    det = H[0][0];
+  } else if constexpr (DR == 2) {
+    det = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+  } else {
+    det = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) - H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+          H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+  }
+  return spd_solve<DR, T>(H, b, s) && det > rel_det * dprod;
+}
+
 // The mixed-precision lane loop over a source of work (see find_f64.cuh).
 template <int N, int D, int DR, class Work>
 __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B, int* __restrict__ queue,
@@ -212,45 +247,35 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
       // manifold and not zero, and the stationary point G^T dx = 0 moves by
       // |dx| times the Jacobian's error, so there G is evaluated in FP64.
       constexpr bool kG64 = DR < D;
-      double xv[D], dxd[D], Gd[D * DR];
+      double xv[D], dxd[D], Gd[kG64 ? D * DR : 1];
       eval_xG<N, D, DR, kG64, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, r64, ts64, xv,
                                       kG64 ? Gd : nullptr);
 #pragma unroll
       for (int c = 0; c < D; ++c) dxd[c] = xs[c] - xv[c];
-      if constexpr (!kG64) {
+      double s[DR];
+      bool ok;
+      if constexpr (kG64) {
+        ok = gauss_newton_step<D, DR, double>(Gd, dxd, 1e-8, s);
+      } else {
+        // Iterative refinement: the residual in FP64, the correction from
+        // the FP32 Jacobian solved in FP32.  The correction's relative error
+        // (about cond(G) times the FP32 rounding) only slows the FP64
+        // iteration from quadratic to linear convergence at that rate, so
+        // the FP32 solve is used where G^T G is well enough conditioned
+        // for a rate far below 1 and the FP64 solve otherwise.
+        float d32[D], s32[DR];
 #pragma unroll
-        for (int q2 = 0; q2 < D * DR; ++q2) Gd[q2] = (double)G[q2];
-      }
-      // Gauss-Newton step in FP64: (G^T G) s = G^T dx
-      double H[DR][DR], b[DR], s[DR];
+        for (int c = 0; c < D; ++c) d32[c] = (float)dxd[c];
+        ok = gauss_newton_step<D, DR, float>(G, d32, 1e-3f, s32);
 #pragma unroll
-      for (int j = 0; j < DR; ++j) {
-        double t = 0.0;
+        for (int j = 0; j < DR; ++j) s[j] = (double)s32[j];
+        if (!ok) {
+          double G64[D * DR];
 #pragma unroll
-        for (int c = 0; c < D; ++c) t += Gd[c * DR + j] * dxd[c];
-        b[j] = t;
-#pragma unroll
-        for (int k = 0; k < DR; ++k) {
-          double u = 0.0;
-#pragma unroll
-          for (int c = 0; c < D; ++c) u += Gd[c * DR + j] * Gd[c * DR + k];
-          H[j][k] = u;
+          for (int q2 = 0; q2 < D * DR; ++q2) G64[q2] = (double)G[q2];
+          ok = gauss_newton_step<D, DR, double>(G64, dxd, 1e-8, s);
         }
       }
-      double dprod = 1.0;
-#pragma unroll
-      for (int j = 0; j < DR; ++j) dprod *= H[j][j];
-      double det;
-      if constexpr (DR == 1) {
-        det = H[0][0];
-      } else if constexpr (DR == 2) {
-        det = H[0][0] * H[1][1] - H[0][1] * H[1][0];
-      } else {
-        det = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
-              H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
-              H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
-      }
-      bool ok = spd_solve<DR, double>(H, b, s) && det > 1e-8 * dprod;
       bool inside = ok;
       double mx = 0.0, rnn[DR];
 #pragma unroll
@@ -268,8 +293,17 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           double t = dxd[c];
+          if constexpr (kG64) {
 #pragma unroll
-          for (int j = 0; j < DR; ++j) t -= Gd[c * DR + j] * s[j];
+            for (int j = 0; j < DR; ++j) t -= Gd[c * DR + j] * s[j];
+          } else {
+            // G s is below the Newton tolerance times |G|: FP32 keeps it to
+            // 1e-7 relative, far below the FP64 rounding of dx
+            float gs = 0.f;
+#pragma unroll
+            for (int j = 0; j < DR; ++j) gs = fmaf(G[c * DR + j], (float)s[j], gs);
+            t -= (double)gs;
+          }
           f += t * t;
         }
         if (DR < D && !(f < mp->dist_tol)) {
