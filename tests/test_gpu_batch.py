@@ -135,3 +135,39 @@ def test_batch_cell_order_invariance(fp, torch, config4_small, precision):
     for a, b in zip(*outs):
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+
+
+def test_batch_full_size_sampled(fp, torch):
+    """The full 64-mesh workload (7.3 million points over 645k elements) in the
+    launch configuration the benchmark times (one autotuned graph, FP64 and
+    mixed): on seven of the meshes, chosen across types, orders and sizes,
+    400 points spread over each point set match the oracle (code and element
+    exactly, r and dist2 to the FP64 tolerance, the interpolated field
+    relative to the field's scale)."""
+    ws = W.config4()
+    pick = ["m16_hex3d_n15_p7", "m42_hex3d_n18_p5", "m33_hex3d_n17_p4", "m0_sphere_n35_p7",
+            "m61_torus_84x28_p3", "m6_quad2d_n33_p7", "m52_quad2d_n38_p4"]
+    by_name = {w.name: i for i, w in enumerate(ws)}
+    assert all(p in by_name for p in pick)
+    meshes = [fp.Mesh(torch.from_numpy(w.coords).cuda(), w.d, w.dr, w.order) for w in ws]
+    entries = [(m, torch.from_numpy(w.pts).cuda(), torch.from_numpy(w.field).cuda()) for m, w in zip(meshes, ws)]
+    oms = {p: oracle.OracleMesh(ws[by_name[p]].coords, ws[by_name[p]].d, ws[by_name[p]].dr, ws[by_name[p]].N)
+           for p in pick}
+    for prec in (fp.FP_F64, fp.FP_MIXED):
+        b = fp.Batch(entries, prec)
+        b.autotune()
+        b.run()
+        torch.cuda.synchronize()
+        for p in pick:
+            i = by_name[p]
+            w, om = ws[i], oms[p]
+            sel = np.linspace(0, len(w.pts) - 1, 400).astype(np.int64)
+            got = tuple(to_np(t)[sel] for t in b.outputs[i][:4])
+            o = om.findpts(w.pts[sel])
+            compare_find(o, got, label=f"full batch {prec} {p}", xscale=1.3, om=om, pts=w.pts[sel])
+            u = to_np(b.outputs[i][4])[..., sel]
+            compare_eval(w.field, om.NE, w.N ** w.dr, o[1], om.eval(w.field, *o[:3]), u, p + " eval")
+        b.close()
+    for m in meshes:
+        assert m.device_status() == 0
+        m.close()
