@@ -179,7 +179,7 @@ int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r
 /* Find, and optionally Interpolate, end to end from host memory.  The paper
  * has no counterpart: it is fp_findpts followed by fp_eval, with the points
  * copied to the device and the results copied back in chunks of `chunk`
- * points (0: automatic, four chunks of at least 2^21 points), each chunk's
+ * points (0: automatic, chunks of n/4 points, at least 2^19), each chunk's
  * copies overlapping the search of the others, and consecutive chunks
  * searched on two streams so that one's launch fills the other's tail.
  *   pts_host [n][d]; outputs code_host [n], elem_host [n], r_host [n][dr],

@@ -1,13 +1,15 @@
 // fp_findpts_host: Find (and Interpolate) end to end from host memory, with
-// the host<->device copies of one chunk of points overlapping the search of
-// another.
+// the host<->device copies of some chunks of points overlapping the search
+// of others.
 //
-// Chunk k's points go to the device on a copy stream; a compute stream (the
-// caller's for even k, a second one for odd k) waits for them, searches the
-// chunk (fp_findpts, with its cell order) and interpolates the field
-// (fp_eval); the copy stream then waits for that and brings the chunk's
-// results back while the next chunk is searched.  Only the first upload and
-// the last download are not hidden behind kernels.  Two compute streams let
+// Every chunk's points go to the device on an upload stream, all issued up
+// front; a compute stream (the caller's for even k, a second one for odd k)
+// waits for chunk k's upload, searches the chunk (fp_findpts, with its cell
+// order) and interpolates the field (fp_eval); a download stream waits for
+// that and brings the chunk's results back.  Uploads and downloads run on
+// separate streams so that they use both directions of the link at once and
+// neither waits behind the other; only the first chunk's upload and the last
+// chunk's download are not hidden behind kernels.  Two compute streams let
 // the next chunk's persistent find launch take the SMs that the current one
 // leaves during its tail (its last points run with few lanes), which a
 // single stream would leave idle.
@@ -19,13 +21,16 @@
 
 namespace {
 
-// Each chunk costs the tail of its find launch (about half a millisecond at
-// 10^6 points) and saves the copy time of a chunk (about a millisecond per
-// 10^6 points in and out), so chunking pays only for large calls: four
-// chunks, at least 2^21 points each (one chunk below 2^22 points).
+// Each chunk adds the tail of its find launch (a few tenths of a
+// millisecond, partly hidden by the other compute stream) and hides the
+// copies of all but the first upload and the last download (about 1.3 ms
+// per 10^6 points in and out).  Measured on the 32^3 p=4 hex mesh: two
+// chunks are best at 10^6 points (13.6 against 14.2 ms for one), three or
+// four at 4x10^6 (51.8 against 55.2 ms); so chunks of n/4 points, at least
+// 2^19.
 int64_t auto_chunk(int64_t n) {
   const int64_t c = (n + 3) / 4;
-  return c < ((int64_t)1 << 21) ? ((int64_t)1 << 21) : c;
+  return c < ((int64_t)1 << 19) ? ((int64_t)1 << 19) : c;
 }
 
 }  // namespace
@@ -54,24 +59,35 @@ extern "C" int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int
   double* out = dist2 + n;  // [K][nc][C]: each chunk's values together
   int32_t* code = (int32_t*)(out + (size_t)nc * n);
   int32_t* elem = code + n;
-  cudaStream_t cp = nullptr, c1 = nullptr;
-  std::vector<cudaEvent_t> ev(2 * K + 2, nullptr);
+  cudaStream_t up = nullptr, down = nullptr, c1 = nullptr;
+  // events: uploaded[k], computed[k], then the start and the three joins
+  std::vector<cudaEvent_t> ev(2 * K + 4, nullptr);
+  cudaEvent_t* uploaded = ev.data();
+  cudaEvent_t* computed = ev.data() + K;
+  cudaEvent_t& start = ev[2 * K];
   int rc = FP_OK;
-  if (cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c1, cudaStreamNonBlocking) != cudaSuccess)
     rc = FP_ELAUNCH;
   for (auto& e : ev)
     if (rc == FP_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = FP_ELAUNCH;
   // the other streams start after the allocation on the caller's stream
-  if (rc == FP_OK && (cudaEventRecord(ev[2 * K], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev[2 * K], 0) != cudaSuccess ||
-                      cudaStreamWaitEvent(c1, ev[2 * K], 0) != cudaSuccess))
+  if (rc == FP_OK && (cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(up, start, 0) != cudaSuccess ||
+                      cudaStreamWaitEvent(down, start, 0) != cudaSuccess ||
+                      cudaStreamWaitEvent(c1, start, 0) != cudaSuccess))
     rc = FP_ELAUNCH;
   for (int64_t k = 0; k < K && rc == FP_OK; ++k) {
     const int64_t off = k * C, len = (n - off < C) ? n - off : C;
-    cudaStream_t cs = (k % 2 == 0) ? st : c1;
     if (cudaMemcpyAsync(pts + off * d, pts_host + off * d, sizeof(double) * len * d, cudaMemcpyHostToDevice,
-                        cp) != cudaSuccess ||
-        cudaEventRecord(ev[2 * k], cp) != cudaSuccess || cudaStreamWaitEvent(cs, ev[2 * k], 0) != cudaSuccess) {
+                        up) != cudaSuccess ||
+        cudaEventRecord(uploaded[k], up) != cudaSuccess)
+      rc = FP_ELAUNCH;
+  }
+  for (int64_t k = 0; k < K && rc == FP_OK; ++k) {
+    const int64_t off = k * C, len = (n - off < C) ? n - off : C;
+    cudaStream_t cs = (k % 2 == 0) ? st : c1;
+    if (cudaStreamWaitEvent(cs, uploaded[k], 0) != cudaSuccess) {
       rc = FP_ELAUNCH;
       break;
     }
@@ -79,31 +95,33 @@ extern "C" int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int
     double* o = out + (size_t)nc * off;
     if (rc == FP_OK && nc > 0) rc = fp_eval(m, code + off, elem + off, r + off * dr, len, field_dev, nc, o, cs);
     if (rc != FP_OK) break;
-    if (cudaEventRecord(ev[2 * k + 1], cs) != cudaSuccess || cudaStreamWaitEvent(cp, ev[2 * k + 1], 0) != cudaSuccess) {
+    if (cudaEventRecord(computed[k], cs) != cudaSuccess || cudaStreamWaitEvent(down, computed[k], 0) != cudaSuccess) {
       rc = FP_ELAUNCH;
       break;
     }
-    cudaError_t e = cudaMemcpyAsync(code_host + off, code + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, cp);
+    cudaError_t e = cudaMemcpyAsync(code_host + off, code + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, down);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(elem_host + off, elem + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, cp);
+      e = cudaMemcpyAsync(elem_host + off, elem + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, down);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(r_host + off * dr, r + off * dr, sizeof(double) * len * dr, cudaMemcpyDeviceToHost, cp);
+      e = cudaMemcpyAsync(r_host + off * dr, r + off * dr, sizeof(double) * len * dr, cudaMemcpyDeviceToHost, down);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dist2_host + off, dist2 + off, sizeof(double) * len, cudaMemcpyDeviceToHost, cp);
+      e = cudaMemcpyAsync(dist2_host + off, dist2 + off, sizeof(double) * len, cudaMemcpyDeviceToHost, down);
     if (e == cudaSuccess && nc > 0)  // [nc][len] on the device into rows of [nc][n]
       e = cudaMemcpy2DAsync(out_host + off, sizeof(double) * n, o, sizeof(double) * len, sizeof(double) * len, nc,
-                            cudaMemcpyDeviceToHost, cp);
+                            cudaMemcpyDeviceToHost, down);
     if (e != cudaSuccess) rc = FP_ELAUNCH;
   }
   // whatever happened, the buffer is freed after every copy and kernel
   if (c1 && cudaEventRecord(ev[2 * K + 1], c1) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K + 1], 0);
-  if (cp && cudaEventRecord(ev[2 * K], cp) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K], 0);
+  if (up && cudaEventRecord(ev[2 * K + 2], up) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K + 2], 0);
+  if (down && cudaEventRecord(ev[2 * K + 3], down) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K + 3], 0);
   cudaFreeAsync(buf, st);
   const cudaError_t es = cudaStreamSynchronize(st);
   if (rc == FP_OK && es != cudaSuccess) rc = FP_ELAUNCH;
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
-  if (cp) cudaStreamDestroy(cp);
+  if (up) cudaStreamDestroy(up);
+  if (down) cudaStreamDestroy(down);
   if (c1) cudaStreamDestroy(c1);
   return rc;
 }
