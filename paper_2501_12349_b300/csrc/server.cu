@@ -17,9 +17,9 @@
 // per shape and one particle-advance launch; up to two ticks are in flight,
 // and a request's stage ends when all its tiles have finished.  Requests are
 // admitted when a first-fit arena inside a fixed device-memory budget and a
-// slot are free; host<->device copies run on a separate copy stream, so
-// arriving requests' uploads and finished requests' downloads overlap the
-// ticks.  Every device wait on the host is bounded (poll + sleep with a
+// slot are free; host<->device copies run on an upload and a download
+// stream of their own, so arriving requests' uploads and finished requests'
+// downloads overlap the ticks and each other (the link's two directions).  Every device wait on the host is bounded (poll + sleep with a
 // deadline); a tick that exceeds it fails its requests with FP_ETIMEDOUT.
 #include <stdlib.h>
 #include <string.h>
@@ -225,7 +225,7 @@ struct fp_server_s {
   std::vector<fp::MeshEntry> meshes;
   fp_server_opts opts;
   fp::Arena arena;
-  cudaStream_t copy = nullptr;
+  cudaStream_t up = nullptr, down = nullptr;
   fp::TickSlot slot[2];
   int max_items = 0;
   int64_t tick_points = 0;
@@ -293,10 +293,10 @@ void admit(fp_server_s* s) {
     q.block = (char*)blk;
     carve(s, q);
     const int d = s->meshes[q.mesh].m->d;
-    cudaError_t e = cudaMemcpyAsync(q.x, q.pts_h, sizeof(double) * q.n * d, cudaMemcpyHostToDevice, s->copy);
+    cudaError_t e = cudaMemcpyAsync(q.x, q.pts_h, sizeof(double) * q.n * d, cudaMemcpyHostToDevice, s->up);
     if (e == cudaSuccess && q.kind == FP_REQ_PARTICLE)
-      e = cudaMemcpyAsync(q.xs, q.x, sizeof(double) * q.n * d, cudaMemcpyDeviceToDevice, s->copy);
-    if (e == cudaSuccess) e = cudaEventRecord(q.ev, s->copy);
+      e = cudaMemcpyAsync(q.xs, q.x, sizeof(double) * q.n * d, cudaMemcpyDeviceToDevice, s->up);
+    if (e == cudaSuccess) e = cudaEventRecord(q.ev, s->up);
     q.status = e == cudaSuccess ? FP_OK : FP_ELAUNCH;
     q.state = R_UPLOADING;
     q.t_admit = Clock::now();
@@ -321,13 +321,13 @@ void finish(fp_server_s* s, Request& q, int status) {
   s->cv_done.notify_all();
 }
 
-// Copies a request's results to its host buffers on the copy stream.
+// Copies a request's results to its host buffers on the download stream.
 void start_download(fp_server_s* s, Request& q) {
   const MeshEntry& me = s->meshes[q.mesh];
   const int d = me.m->d, dr = me.m->dr;
   cudaError_t e = cudaSuccess;
   auto cp = [&](void* h, const void* dv, size_t bytes) {
-    if (h && e == cudaSuccess) e = cudaMemcpyAsync(h, dv, bytes, cudaMemcpyDeviceToHost, s->copy);
+    if (h && e == cudaSuccess) e = cudaMemcpyAsync(h, dv, bytes, cudaMemcpyDeviceToHost, s->down);
   };
   cp(q.code_h, q.code, sizeof(int32_t) * q.n);
   cp(q.elem_h, q.elem, sizeof(int32_t) * q.n);
@@ -335,7 +335,7 @@ void start_download(fp_server_s* s, Request& q) {
   cp(q.dist2_h, q.dist2, sizeof(double) * q.n);
   if (q.kind == FP_REQ_REMAP) cp(q.out_h, q.u, sizeof(double) * q.n * q.nc);
   else cp(q.out_h, q.x, sizeof(double) * q.n * d);
-  if (e == cudaSuccess) e = cudaEventRecord(q.ev, s->copy);
+  if (e == cudaSuccess) e = cudaEventRecord(q.ev, s->down);
   if (e != cudaSuccess) q.status = FP_ELAUNCH;
   q.state = R_DOWNLOADING;
 }
@@ -596,7 +596,8 @@ void destroy_server(fp_server_s* s) {
   }
   for (auto& kv : s->reqs)
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
-  if (s->copy) cudaStreamDestroy(s->copy);
+  if (s->up) cudaStreamDestroy(s->up);
+  if (s->down) cudaStreamDestroy(s->down);
   cudaFree(s->arena.base);
 }
 
@@ -645,7 +646,9 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
   const int64_t ocap = batch_cell_order_ints(std::min(qcap, o.tick_points), all_buckets);
   int rc = FP_OK;
   if (!s->arena.init(o.mem_budget)) rc = FP_ENOMEM;
-  if (rc == FP_OK && cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess) rc = FP_ELAUNCH;
+  if (rc == FP_OK && (cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaStreamCreateWithFlags(&s->down, cudaStreamNonBlocking) != cudaSuccess))
+    rc = FP_ELAUNCH;
   for (auto& t : s->slot) {
     if (rc != FP_OK) break;
     t.queue_cap = qcap;
