@@ -40,7 +40,7 @@ WORKLOAD = "hex3d_32^3_p4_kershaw0.3_1e6pts"
 # DRAM bytes (read + write) of one k_find_f64 launch on the 32^3 p=4 mesh with
 # 10^6 points, from one ncu capture of the current kernel (the summary under
 # profiles/ gives the command); None once the kernel changes.
-F64_TRAFFIC = 853.5e6
+F64_TRAFFIC = 868.4e6
 
 
 def flop_terms(N, d, dr):
@@ -59,26 +59,28 @@ def flop_terms(N, d, dr):
         hess = d * 2 * N + 12 * N + 2 * d
         eval_x = 2 * (N ** 2 + N) + dr * 4 * N
     return {"eval_g": eval_g, "hess": hess, "eval_x": eval_x, "box": 2 * d * d + d,
-            "node": 3 * d * ne, "newton": 60, "basis": dr * 4 * N}
+            "node": 3 * d * ne, "newton": 60, "basis": dr * 4 * N,
+            "node_start": 2 * d * dr * N + 3 * d, "linear_start": 2 * d * dr}
 
 
-def find_flops(stats, N, d, dr, node=True):
+def find_flops(stats, N, d, dr, start="node"):
     """Algorithmic flops of a find from its counters: candidates C, Newton
-    steps I, steps with the beta term B, evaluations of x and G (one per
-    candidate and one per trial step; re-evaluations after rejected steps
-    are not counted)."""
+    steps I, steps with the beta term B, full evaluations EV of x and G (re-
+    evaluations after rejected steps are not counted).  start: "node" (the
+    FP64 kernel: x at the closest node is the node, G one N-term sum per
+    direction; the search itself runs on the FP32 pipe and is not counted;
+    EV = one per trial step) or "linear" (the mixed kernel's FP32 phase:
+    r0 from the linearised map, then a full evaluation; EV counts it)."""
     t = flop_terms(N, d, dr)
     C, I, B, EV = int(stats[0]), int(stats[1]), int(stats[3]), int(stats[7])
-    return C * (t["box"] + (t["node"] if node else 0)) + EV * t["eval_g"] + I * t["newton"] + B * t["hess"]
+    return C * (t["box"] + t[start + "_start"]) + EV * t["eval_g"] + I * t["newton"] + B * t["hess"]
 
 
 def flop_model(stats, N, d, dr, n_found, nc):
     """Algorithmic FP64 flops of one find launch and one eval launch."""
     t = flop_terms(N, d, dr)
     ev = n_found * (nc * (t["eval_x"] - t["basis"]) + t["basis"])
-    # the closest-node search runs on the FP32 pipe (certified, FP64 only
-    # inside its rounding margin), so it is not counted as FP64 work
-    return float(find_flops(stats, N, d, dr, node=False)), float(ev)
+    return float(find_flops(stats, N, d, dr, "node")), float(ev)
 
 
 def mixed_flop_model(stats, N, d, dr):
@@ -90,14 +92,14 @@ def mixed_flop_model(stats, N, d, dr):
     FP64 kernel on the handed-over points (counters [8]-[15])."""
     t = flop_terms(N, d, dr)
     C, R = int(stats[0]), int(stats[4])
-    f32 = C * 2 * d * dr + find_flops(stats[0:8], N, d, dr, node=False)
+    f32 = find_flops(stats[0:8], N, d, dr, "linear")
     refine = d * (t["eval_x"] - t["basis"]) + t["basis"] + 2 * d
     solve = 2 * d * dr * (dr + 1) + 30
     if dr == d:
         f32 += R * solve
     else:
         refine += solve
-    f64 = R * refine + find_flops(stats[8:16], N, d, dr, node=False)
+    f64 = R * refine + find_flops(stats[8:16], N, d, dr, "node")
     return float(f32), float(f64)
 
 
@@ -274,7 +276,7 @@ def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, peaks):
         outs[prec] = (code.clone(), elem.clone(), r.clone())
         fsec = statistics.mean(fms) / 1e3
         if prec == "f64":
-            f32, f64 = 0.0, find_flops(sv, w.N, 3, 3, node=False)
+            f32, f64 = 0.0, find_flops(sv, w.N, 3, 3, "node")
         else:
             f32, f64 = mixed_flop_model(sv, w.N, 3, 3)
         res[prec] = {"value": world * n * steps / t, "unit": "points/s",

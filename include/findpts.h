@@ -137,8 +137,11 @@ int fp_findpts(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
  *   [2] rejected trust-region steps            [3] Newton steps with beta = 1
  *   [4] FP64 refinement evaluations (mixed)    [5] box tests decided in FP64
  *   [6] points the mixed path handed to its FP64 kernel
- *   [7] evaluations of x(r) and G(r): one per candidate plus one per trial
- *       step (re-evaluations after a rejected step are not counted)
+ *   [7] full evaluations of x(r) and G(r), re-evaluations after a rejected
+ *       step not counted: in the FP64 kernel one per trial step (a
+ *       candidate starts at its closest GLL node, where x is the node and G
+ *       one N-term sum per direction); in the mixed path's FP32 kernel also
+ *       one per candidate, at its linearised start
  * With FP_MIXED, [0]-[7] count the FP32 kernel (its iterations are FP32
  * iterations) and [8]-[15] count, in the same layout, the FP64 kernel that
  * finishes the points of [6]; with FP_F64, [8]-[15] stay zero. */

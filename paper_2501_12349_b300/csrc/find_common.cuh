@@ -317,6 +317,35 @@ __device__ __forceinline__ void node_coords(const BasisTab& B, int n, T (&r)[DR]
   }
 }
 
+// x and G at the GLL node nb of element e, the start r0 of Newton: the
+// Lagrange basis is a unit vector at a node, so x is the node's coordinates,
+// and column j of G is the derivative along the node's grid line in
+// direction j, an N-term sum with the differentiation matrix dn (row
+// dn + i*N, i the node's index in direction j).
+template <int N, int D, int DR>
+__device__ __forceinline__ void node_start(const DevMesh& m, int e, int nb, const double* __restrict__ dn,
+                                           double (&x)[D], double (&G)[D * DR]) {
+  constexpr int NN = ipow(N, DR);
+  const double* X = m.coords + (int64_t)e * NN;
+  const int64_t cs = m.cstride;
+  const int idx[3] = {nb % N, (nb / N) % N, nb / (N * N)};
+#pragma unroll
+  for (int c = 0; c < D; ++c) x[c] = __ldg(X + c * cs + nb);
+#pragma unroll
+  for (int j = 0; j < DR; ++j) {
+    const int st = j == 0 ? 1 : (j == 1 ? N : N * N);
+    const double* line = X + (nb - idx[j] * st);
+    const double* row = dn + idx[j] * N;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double g = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) g = fma(__ldg(line + c * cs + k * st), row[k], g);
+      G[c * DR + j] = g;
+    }
+  }
+}
+
 template <int D>
 __device__ __forceinline__ double aabb_scale(const DevMesh& m, int64_t e) {
   double X = 0.0;

@@ -8,8 +8,13 @@
 //    (point, candidate, Newton iteration) states and pulls the next point
 //    from a per-CTA counter, so no lane idles while its warp has work;
 //  * each round of the loop has one warp-uniform site where every busy lane
-//    evaluates x(r) and G(r) of its current element (the sum-factorised
-//    contraction that is most of the FP64 work), inlined once;
+//    evaluates x(r) and G(r) of its current element at a trial point (the
+//    sum-factorised contraction that is most of the FP64 work), inlined once;
+//  * a candidate starts at its closest GLL node, where x is the node itself
+//    and G takes N terms per direction: the lanes that start one do it right
+//    after the warp's node search and take their first Newton step in a
+//    second bookkeeping pass, so their first full evaluation is already a
+//    trial step;
 //  * the box tests and the closest-node search, done by whichever lanes
 //    start a candidate, run in FP32 with rigorous rounding margins and fall
 //    back to FP64 only inside the margin, so every decision equals the FP64
@@ -20,8 +25,8 @@
 
 namespace fp {
 
-enum : int { M_IDLE = 0, M_SCAN = 1, M_NEWTON = 2, M_RESTORE = 3, M_DONE = 4 };
-enum : int { E_INIT = 1, E_TRIAL = 2, E_RESTORE = 3 };
+enum : int { M_IDLE = 0, M_SCAN = 1, M_START = 2, M_NEWTON = 3, M_RESTORE = 4, M_DONE = 5 };
+enum : int { E_TRIAL = 1, E_RESTORE = 2 };
 
 // The FP64 lane loop over a source of work (SingleWork or BatchWork); all
 // meshes of one launch share N, D, DR and so the basis table B.
@@ -31,10 +36,15 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
   __shared__ double s_slab[DR == 3 ? 2 * N * kFindThreads : 1];
   __shared__ double s_hs[beta_entries<DR>() * kFindThreads];
   __shared__ double s_bscr[(kFindThreads / 32) * kBetaScratch];
+  __shared__ double s_dn[N * N];
   const TSlots<N, double> ts{s_slab};
   double* const wscr = s_bscr + (threadIdx.x >> 5) * kBetaScratch;
   __shared__ unsigned long long s_next;
-  if (threadIdx.x == 0) s_next = 0;
+  if (threadIdx.x == 0) {
+    s_next = 0;
+#pragma unroll
+    for (int i = 0; i < N * N; ++i) s_dn[i] = B.dn[i];
+  }
   __syncthreads();
   Counters cnt;
   const int64_t n = w.n;
@@ -42,7 +52,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
   const int64_t nchunks = (n + (1 << clog2) - 1) >> clog2;
   const DevMesh* mp = w.first();
   int item = 0;
-  int mode = M_IDLE, etype = E_INIT;
+  int mode = M_IDLE, etype = E_TRIAL;
   int64_t pi = 0;
   double xs[D];
   float x32[D];
@@ -57,128 +67,148 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
   for (int j = 0; j < DR; ++j) br[j] = r[j] = rn[j] = 0.0;
 
   while (true) {
-    bool need = false;
-    // ---- per-lane bookkeeping until this lane needs one evaluation --------
-    while (mode != M_DONE && !need) {
-      if (++guard > (1u << 26)) {
-        record_status(mp->status, FP_DEV_SPIN_CAP);
-        mode = M_DONE;
-        break;
-      }
-      if (mode == M_IDLE) {
-        const unsigned long long s = atomicAdd(&s_next, 1ull);
-        const int64_t chunk = (int64_t)(s >> clog2) * gridDim.x + blockIdx.x;
-        if (chunk >= nchunks) {
+    bool need = false, finished = false;
+    for (int pass = 0;; ++pass) {
+      // ---- per-lane bookkeeping until this lane needs an evaluation or a start
+      while (mode != M_DONE && mode != M_START && !need) {
+        if (++guard > (1u << 26)) {
+          record_status(mp->status, FP_DEV_SPIN_CAP);
           mode = M_DONE;
           break;
         }
-        const int64_t g = (chunk << clog2) + (int64_t)(s & ((1u << clog2) - 1));
-        if (g >= n) continue;
-        w.locate(g, mp, item, pi);
-        w.load(item, pi, xs);
+        if (mode == M_IDLE) {
+          const unsigned long long s = atomicAdd(&s_next, 1ull);
+          const int64_t chunk = (int64_t)(s >> clog2) * gridDim.x + blockIdx.x;
+          if (chunk >= nchunks) {
+            mode = M_DONE;
+            break;
+          }
+          const int64_t g = (chunk << clog2) + (int64_t)(s & ((1u << clog2) - 1));
+          if (g >= n) continue;
+          w.locate(g, mp, item, pi);
+          w.load(item, pi, xs);
 #pragma unroll
-        for (int c = 0; c < D; ++c) x32[c] = (float)xs[c];
-        bcode = FP_NOT_FOUND;
-        be = -1;
-        bd = INFINITY;
+          for (int c = 0; c < D; ++c) x32[c] = (float)xs[c];
+          bcode = FP_NOT_FOUND;
+          be = -1;
+          bd = INFINITY;
 #pragma unroll
-        for (int j = 0; j < DR; ++j) br[j] = 0.0;
-        const int64_t cell = point_cell<D>(*mp, xs);
-        if (cell < 0) {
-          w.write(item, pi, bcode, be, br, bd);
-          continue;
+          for (int j = 0; j < DR; ++j) br[j] = 0.0;
+          const int64_t cell = point_cell<D>(*mp, xs);
+          if (cell < 0) {
+            w.write(item, pi, bcode, be, br, bd);
+            continue;
+          }
+          q = __ldg(mp->cell_start + cell);
+          qend = __ldg(mp->cell_start + cell + 1);
+          mode = M_SCAN;
         }
-        q = __ldg(mp->cell_start + cell);
-        qend = __ldg(mp->cell_start + cell + 1);
-        mode = M_SCAN;
-      }
-      if (mode == M_SCAN) {
-        e = next_candidate<D>(*mp, xs, x32, q, qend, cnt);
-        if (e < 0) {
-          w.write(item, pi, bcode, be, br, bd);
-          mode = M_IDLE;
-          continue;
+        if (mode == M_SCAN) {
+          e = next_candidate<D>(*mp, xs, x32, q, qend, cnt);
+          if (e < 0) {
+            w.write(item, pi, bcode, be, br, bd);
+            mode = M_IDLE;
+            continue;
+          }
+          ++cnt.v[0];
+          xscale = aabb_scale<D>(*mp, e);
+          mode = M_START;  // the start r0, the closest node, is found by the warp below
+          break;
         }
-        ++cnt.v[0];
-        xscale = aabb_scale<D>(*mp, e);
-        etype = E_INIT;  // the start r0, the closest node, is found by the warp below
-        need = true;
-        break;
-      }
-      if (mode == M_RESTORE) {
-        etype = E_RESTORE;
-        need = true;
-        break;
-      }
-      // mode == M_NEWTON: one step of Sec. 3.2.1 from (r, dx, G, F, alpha)
-      bool done = false;
-      if (l >= mp->max_iter) {
-        done = true;
-      } else {
-        const bool beta = (l > 0) && at_bound<DR>(r);
-        double HS[DR][DR] = {};
-        if (beta) {
-          beta_load<DR, double>(s_hs, HS);  // computed by the warp after the last evaluation
-          ++cnt.v[3];
+        if (mode == M_RESTORE) {
+          etype = E_RESTORE;
+          need = true;
+          break;
         }
-        double ds[DR];
-        bool used_beta;
-        const double mx = newton_step<D, DR>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
-        if (mx < mp->newton_tol) {
-          // the last step is taken; dist2 from the linear model at r
-          F = model_dist2<D, DR>(G, dx, ds);
-#pragma unroll
-          for (int j = 0; j < DR; ++j) r[j] = rn[j];
-          ++cnt.v[1];
+        // mode == M_NEWTON: one step of Sec. 3.2.1 from (r, dx, G, F, alpha)
+        bool done = false;
+        if (l >= mp->max_iter) {
           done = true;
         } else {
-          pred = predicted_decrease<D, DR>(G, dx, ds, used_beta, HS);
-          if (!(pred > 0.0)) {
+          const bool beta = (l > 0) && at_bound<DR>(r);
+          double HS[DR][DR] = {};
+          if (beta) {
+            beta_load<DR, double>(s_hs, HS);  // computed by the warp after the last evaluation
+            ++cnt.v[3];
+          }
+          double ds[DR];
+          bool used_beta;
+          const double mx = newton_step<D, DR>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
+          if (mx < mp->newton_tol) {
+            // the last step is taken; dist2 from the linear model at r
+            F = model_dist2<D, DR>(G, dx, ds);
+#pragma unroll
+            for (int j = 0; j < DR; ++j) r[j] = rn[j];
+            ++cnt.v[1];
             done = true;
           } else {
-            ++cnt.v[1];
-            etype = E_TRIAL;
-            need = true;
+            pred = predicted_decrease<D, DR>(G, dx, ds, used_beta, HS);
+            if (!(pred > 0.0)) {
+              done = true;
+            } else {
+              ++cnt.v[1];
+              etype = E_TRIAL;
+              need = true;
+            }
+          }
+        }
+        if (done) {
+          bool inside = true;
+#pragma unroll
+          for (int j = 0; j < DR; ++j) inside &= below_unit(r[j]);
+          if (DR < D) inside &= F < mp->dist_tol;
+          if (inside || F < bd) {
+            bcode = inside ? FP_INTERIOR : FP_BORDER;
+            be = e;
+            bd = F;
+#pragma unroll
+            for (int j = 0; j < DR; ++j) br[j] = r[j];
+          }
+          if (inside) {
+            w.write(item, pi, bcode, be, br, bd);
+            mode = M_IDLE;
+          } else {
+            mode = M_SCAN;
           }
         }
       }
-      if (done) {
-        bool inside = true;
-#pragma unroll
-        for (int j = 0; j < DR; ++j) inside &= below_unit(r[j]);
-        if (DR < D) inside &= F < mp->dist_tol;
-        if (inside || F < bd) {
-          bcode = inside ? FP_INTERIOR : FP_BORDER;
-          be = e;
-          bd = F;
-#pragma unroll
-          for (int j = 0; j < DR; ++j) br[j] = r[j];
-        }
-        if (inside) {
-          w.write(item, pi, bcode, be, br, bd);
-          mode = M_IDLE;
-        } else {
-          mode = M_SCAN;
-        }
+      // a lane that starts another candidate in the second pass waits for
+      // the next round's node search
+      if (pass == 1) break;
+      if (__all_sync(0xffffffffu, mode == M_DONE)) {
+        finished = true;
+        break;
       }
-    }
-    if (__all_sync(0xffffffffu, mode == M_DONE)) break;
-    // ---- warp-uniform closest-node search for the lanes that start a candidate
-    {
-      const bool start = need && etype == E_INIT;
+      // ---- warp-uniform closest-node search, then the start at that node
+      const bool start = mode == M_START;
+      if (!__any_sync(0xffffffffu, start)) break;
       float xr[D];
       if (start) rel_point<D>(*mp, e, xs, xr);
       int nb = 0;
       closest_node_warp<N, D, DR>(start, *mp, e, xs, xr, nb);
-      if (start) node_coords<N, DR>(B, nb, r);
+      if (start) {
+        node_coords<N, DR>(B, nb, r);
+        double xv[D];
+        node_start<N, D, DR>(*mp, e, nb, s_dn, xv, G);
+        F = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          dx[c] = xs[c] - xv[c];
+          F += dx[c] * dx[c];
+        }
+        alpha = 1.0;
+        l = 0;
+        mode = M_NEWTON;
+      }
     }
+    if (finished) break;
     // ---- warp-uniform evaluation of x(r) and G(r) -------------------------
     if (need) {
       double re[DR];
 #pragma unroll
       for (int j = 0; j < DR; ++j) re[j] = (etype == E_TRIAL) ? rn[j] : r[j];
       double xv[D];
-      if (etype != E_RESTORE) ++cnt.v[7];
+      if (etype == E_TRIAL) ++cnt.v[7];
       eval_xG<N, D, DR, true, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, re, ts, xv, G);
       double Fn = 0.0;
 #pragma unroll
@@ -198,10 +228,6 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
           mode = M_RESTORE;  // dx and G now belong to rn: re-evaluate at r
         }
       } else {
-        if (etype == E_INIT) {
-          alpha = 1.0;
-          l = 0;
-        }
         F = Fn;
         mode = M_NEWTON;
       }

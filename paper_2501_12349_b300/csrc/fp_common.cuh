@@ -51,6 +51,7 @@ struct BasisTab {
   double w[FP_MAX_N];
   float zf[FP_MAX_N];
   float wf[FP_MAX_N];
+  double dn[FP_MAX_N * FP_MAX_N];  // dn[i * N + m] = phi_m'(z_i), the GLL differentiation matrix
 };
 
 // Everything a find / eval kernel reads about a mesh (passed by value).

@@ -97,6 +97,20 @@ int host_basis_tab(int N, BasisTab* tab) {
     tab->zf[i] = (float)z[i];
     tab->wf[i] = (float)(1.0 / p);
   }
+  // phi_m'(z_i) = (w_m / w_i) / (z_i - z_m) for m != i (differentiate the
+  // product form of phi_m at a root of its other factors); the diagonal is
+  // minus the row's other entries, since the derivative of sum_m phi_m = 1
+  // vanishes.
+  for (int i = 0; i < N; ++i) {
+    double diag = 0.0;
+    for (int m = 0; m < N; ++m) {
+      if (m == i) continue;
+      const double v = (tab->w[m] / tab->w[i]) / (z[i] - z[m]);
+      tab->dn[i * N + m] = v;
+      diag -= v;
+    }
+    tab->dn[i * N + i] = diag;
+  }
   return FP_OK;
 }
 
