@@ -13,7 +13,7 @@ int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, 
     constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
     const int blocks = persistent_blocks(n, f64_ctas(N));
     k_find_f64<N, D, DR><<<blocks, kFindThreads, 0, st>>>(v, m->basis, pts, pidx, n, nullptr, code,
-                                                          elem, r, dist2, stats);
+                                                          elem, r, dist2, 5, stats);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
   });
 }

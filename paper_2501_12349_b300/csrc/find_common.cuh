@@ -57,6 +57,15 @@ inline int sm_count() {
 }
 
 // Persistent grid: per_sm CTAs per SM, fewer when n is small.
+// The FP64 kernel over the points a mixed launch hands over (about 1% of
+// them) takes as long as its slowest points, each a chain of full-warp FP64
+// instructions.  In 128-thread CTAs the first warp to ask takes a CTA's
+// whole chunk, so the few busy warps can share one sub-partition's FP64
+// unit; one-warp CTAs with chunks of 4 points spread them over all four.
+constexpr int kFollowThreads = 32;
+constexpr int kFollowClog2 = 2;
+inline int follow_blocks() { return sm_count() * 8; }
+
 inline int persistent_blocks(int64_t n, int per_sm) {
   const int64_t want = (n + kFindThreads - 1) / kFindThreads;
   const int64_t cap = (int64_t)sm_count() * per_sm;

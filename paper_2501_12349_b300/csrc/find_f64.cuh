@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
     k_find_f64(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
                const int* __restrict__ pidx, int64_t n, const int* __restrict__ n_dev,
                int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
-               double* __restrict__ dist2, unsigned long long* stats) {
-  const SingleWork<D, DR> w{&m, pts, pidx, n_dev ? (int64_t)*n_dev : n, code, elem, rout, dist2, 5};
+               double* __restrict__ dist2, int clog2, unsigned long long* stats) {
+  const SingleWork<D, DR> w{&m, pts, pidx, n_dev ? (int64_t)*n_dev : n, code, elem, rout, dist2, clog2};
   find_f64_loop<N, D, DR>(w, B, stats);
 }
 
