@@ -716,10 +716,11 @@ def main():
             "config": {"workload": WORKLOAD, "points_per_gpu": n, "precision": args.precision,
                        "nc": 1, "l2": "flushed (256 MB write) before each timed step",
                        "parallelism": f"replicas{world}"},
-            # per step: the cell order (k_point_cells, k_scan, k_point_scatter),
-            # the find (k_find_f64; mixed: k_find_mixed + k_find_f64 on the
-            # handed-over points) and k_eval_f64
-            "gpu_launches": (5 if args.precision == "f64" else 6) * args.steps,
+            # per step: the cell order (k_point_cells; the bucket scan
+            # k_scan_tiles, k_scan, k_scan_add; k_point_scatter), the find
+            # (k_find_f64; mixed: k_find_mixed + k_find_f64 on the handed-over
+            # points) and k_eval_f64, as the launch list under profiles/ shows
+            "gpu_launches": (7 if args.precision == "f64" else 8) * args.steps,
             "roofline": roofline,
             "kernels_ms": {"find": statistics.mean(find_ms), "eval": statistics.mean(eval_ms)},
             "eval_roofline": {"bound": "alu", "achieved": fl_eval / eval_avg / 1e12, "peak": peak64,
