@@ -451,3 +451,36 @@ def test_findpts_host(fp, torch, chunk, precision):
     for a, b in zip(ref, got2):
         assert torch.equal(a.cpu(), b)
     m.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("case", list(CASES) + ["circle_p3", "helix_p5"])
+def test_points_at_interior_nodes(fp, torch, case, precision):
+    """Points placed at interior GLL nodes of random elements, where the
+    start at the closest node (x the node itself, G from the
+    differentiation matrix) is already the answer: INTERIOR in that element
+    at r = the node, for quads, hexes, surface quads and lines, and equal to
+    the oracle."""
+    if case == "circle_p3":
+        coords, d, dr, order = W.circle_lines(64, 3), 2, 1, 3
+    elif case == "helix_p5":
+        coords, d, dr, order = W.helix_lines(48, 5), 3, 1, 5
+    else:
+        coords, d, dr, order, _ = CASES[case]()
+    N = order + 1
+    om = oracle.OracleMesh(coords, d, dr, N)
+    rng = np.random.default_rng(31)
+    z = W.gll_points(N)[1:-1]
+    el = rng.integers(0, om.NE, 3000).astype(np.int32)
+    rn = z[rng.integers(0, z.size, (3000, dr))]
+    pts = om.forward_map(el, rn)
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    m.set_precision(fp.FP_MIXED if precision == "mixed" else fp.FP_F64)
+    g = gpu_find(torch, m, pts)
+    o = om.findpts(pts)
+    compare_find(o, g, label=f"nodes {case} {precision}", xscale=1.3 * float(np.abs(coords).max()))
+    assert np.all(g[0] == 0), f"{case}: {np.bincount(g[0], minlength=3)}"
+    assert np.array_equal(g[1], el)  # an interior node lies in no other element
+    np.testing.assert_allclose(g[2], rn, atol=1e-10)
+    assert m.device_status() == 0
+    m.close()
