@@ -1,7 +1,7 @@
 // The FP64 find kernel (Sec. 3.2), shared by the FP64 path and by the mixed
 // path, which runs it on the points its FP32 phase could not settle.
 //
-// On this GPU the FP64 FMA pipe (about 1.1 TFLOP/s, 1/62 of FP32) bounds the
+// On this GPU the FP64 FMA pipe (about 1.2 TFLOP/s, 1/62 of FP32) bounds the
 // kernel, and a warp instruction costs the same FP64 issue time whether 1 or
 // 32 lanes are active.  So:
 //  * lanes refill themselves: each lane walks its own sequence of
