@@ -59,9 +59,14 @@ inline int sm_count() {
 // Persistent grid: per_sm CTAs per SM, fewer when n is small.
 // The FP64 kernel over the points a mixed launch hands over (about 1% of
 // them) takes as long as its slowest points, each a chain of full-warp FP64
-// instructions.  In 128-thread CTAs the first warp to ask takes a CTA's
-// whole chunk, so the few busy warps can share one sub-partition's FP64
-// unit; one-warp CTAs with chunks of 4 points spread them over all four.
+// instructions.  Up to kGroupMaxPoints points per launch (a queue of tens
+// of thousands) it runs in group mode, which searches a point's candidate
+// elements side by side; above, the queue is long enough for its total work
+// to count, and the one-lane-per-point loop runs as one-warp CTAs with
+// chunks of 4 points (in 128-thread CTAs the first warp to ask takes the
+// CTA's whole chunk, so the few busy warps can share one sub-partition's
+// FP64 unit).
+constexpr int64_t kGroupMaxPoints = (int64_t)1 << 22;
 constexpr int kFollowThreads = 32;
 constexpr int kFollowClog2 = 2;
 inline int follow_blocks() { return sm_count() * 8; }

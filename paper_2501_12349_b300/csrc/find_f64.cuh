@@ -28,9 +28,87 @@ namespace fp {
 enum : int { M_IDLE = 0, M_SCAN = 1, M_START = 2, M_NEWTON = 3, M_RESTORE = 4, M_DONE = 5 };
 enum : int { E_TRIAL = 1, E_RESTORE = 2 };
 
+// Group mode (kGroup): for launches whose time is the dependency chain of
+// their slowest points rather than their total work (the few points a mixed
+// launch hands over), a warp takes 8 points at a time and gives each 4
+// lanes: slot k = 0, 1, 2 searches the point's k-th candidate element
+// alone, slot 3 the 4th and any later ones in order, so a point's
+// candidates run side by side instead of one after another.  When the whole
+// warp is done the slots merge under the selection rule of Sec. 3.2 (the
+// first INTERIOR in candidate order, else the smallest distance, ties to
+// the earlier candidate), which gives the one-lane result exactly.
+constexpr int kGroupPoints = 8;
+
+// Group mode: the 4 slots of each point merge into its first lane, which
+// writes the point's result.
+template <int DR, class Work>
+__device__ __forceinline__ void group_merge(const Work& w, bool valid, int slot, int item, int64_t pi, int bcode,
+                                            int be, const double (&br)[DR], double bd) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lead = (threadIdx.x & 31) & ~3;
+  int sc = bcode, se = be;
+  double sd = bd, sr[DR];
+#pragma unroll
+  for (int j = 0; j < DR; ++j) sr[j] = br[j];
+  bool fin = sc == FP_INTERIOR;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    const int oc = __shfl_sync(kAll, bcode, lead + k);
+    const int oe = __shfl_sync(kAll, be, lead + k);
+    const double od = __shfl_sync(kAll, bd, lead + k);
+    double orr[DR];
+#pragma unroll
+    for (int j = 0; j < DR; ++j) orr[j] = __shfl_sync(kAll, br[j], lead + k);
+    const bool take = !fin && (oc == FP_INTERIOR || od < sd);
+    fin |= take && oc == FP_INTERIOR;
+    if (take) {
+      sc = oc;
+      se = oe;
+      sd = od;
+#pragma unroll
+      for (int j = 0; j < DR; ++j) sr[j] = orr[j];
+    }
+  }
+  if (valid && slot == 0) w.write(item, pi, sc, se, sr, sd);
+}
+
+// Group mode: the warp takes the next kGroupPoints points of its CTA's
+// chunks (lane l gets point l / 4, slot l % 4) and sets up their cells; a
+// lane without a point waits (M_IDLE), and every lane stops (M_DONE) once
+// the chunks are used up.
+template <int D, int DR, class Work>
+__device__ __forceinline__ void group_fetch(const Work& w, unsigned long long& s_next, int clog2, int64_t nchunks,
+                                            int64_t n, const DevMesh*& mp, int& item, int64_t& pi, double (&xs)[D],
+                                            float (&x32)[D], int& q, int& qend, int& mode, bool& valid) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long s0 = 0;
+  if (lane == 0) s0 = atomicAdd(&s_next, (unsigned long long)kGroupPoints);
+  s0 = __shfl_sync(0xffffffffu, s0, 0);
+  const unsigned long long s = s0 + (unsigned long long)(lane >> 2);
+  const int64_t chunk = (int64_t)(s0 >> clog2) * gridDim.x + blockIdx.x;
+  valid = false;
+  if (chunk >= nchunks) {
+    mode = M_DONE;
+    return;
+  }
+  const int64_t g = (chunk << clog2) + (int64_t)(s & ((1u << clog2) - 1));
+  mode = M_IDLE;
+  if (g >= n) return;
+  valid = true;
+  w.locate(g, mp, item, pi);
+  w.load(item, pi, xs);
+#pragma unroll
+  for (int c = 0; c < D; ++c) x32[c] = (float)xs[c];
+  const int64_t cell = point_cell<D>(*mp, xs);
+  if (cell < 0) return;
+  q = __ldg(mp->cell_start + cell);
+  qend = __ldg(mp->cell_start + cell + 1);
+  mode = M_SCAN;
+}
+
 // The FP64 lane loop over a source of work (SingleWork or BatchWork); all
 // meshes of one launch share N, D, DR and so the basis table B.
-template <int N, int D, int DR, class Work>
+template <int N, int D, int DR, class Work, bool kGroup = false>
 __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, unsigned long long* stats) {
   constexpr int NN = ipow(N, DR);
   __shared__ double s_slab[DR == 3 ? 2 * N * kFindThreads : 1];
@@ -63,14 +141,30 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
   double alpha = 1.0, F = 0.0, pred = 0.0, xscale = 1.0;
   bool clipped = false;
   unsigned guard = 0;
+  [[maybe_unused]] const int slot = threadIdx.x & 3;  // group mode: the lane's candidate slot
+  [[maybe_unused]] int skip = 0;                      // group mode: candidates still to pass over
+  [[maybe_unused]] bool valid = false;                // group mode: the lane holds a point
 #pragma unroll
   for (int j = 0; j < DR; ++j) br[j] = r[j] = rn[j] = 0.0;
 
   while (true) {
+    if constexpr (kGroup) {
+      // the group is done when every lane waits (M_IDLE) or has run out
+      if (__all_sync(0xffffffffu, mode == M_IDLE || mode == M_DONE)) {
+        group_merge<DR>(w, valid, slot, item, pi, bcode, be, br, bd);
+        group_fetch<D, DR>(w, s_next, clog2, nchunks, n, mp, item, pi, xs, x32, q, qend, mode, valid);
+        skip = slot;
+        bcode = FP_NOT_FOUND;
+        be = -1;
+        bd = INFINITY;
+#pragma unroll
+        for (int j = 0; j < DR; ++j) br[j] = 0.0;
+      }
+    }
     bool need = false, finished = false;
     for (int pass = 0;; ++pass) {
       // ---- per-lane bookkeeping until this lane needs an evaluation or a start
-      while (mode != M_DONE && mode != M_START && !need) {
+      while (mode != M_DONE && mode != M_START && !need && !(kGroup && mode == M_IDLE)) {
         if (++guard > (1u << 26)) {
           record_status(mp->status, FP_DEV_SPIN_CAP);
           mode = M_DONE;
@@ -106,9 +200,15 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
         if (mode == M_SCAN) {
           e = next_candidate<D>(*mp, xs, x32, q, qend, cnt);
           if (e < 0) {
-            w.write(item, pi, bcode, be, br, bd);
+            if constexpr (!kGroup) w.write(item, pi, bcode, be, br, bd);
             mode = M_IDLE;
             continue;
+          }
+          if constexpr (kGroup) {
+            if (skip > 0) {  // an earlier slot's candidate
+              --skip;
+              continue;
+            }
           }
           ++cnt.v[0];
           xscale = aabb_scale<D>(*mp, e);
@@ -164,7 +264,9 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
 #pragma unroll
             for (int j = 0; j < DR; ++j) br[j] = r[j];
           }
-          if (inside) {
+          if constexpr (kGroup) {
+            mode = (inside || slot < 3) ? M_IDLE : M_SCAN;
+          } else if (inside) {
             w.write(item, pi, bcode, be, br, bd);
             mode = M_IDLE;
           } else {
@@ -262,6 +364,27 @@ __global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
                      int clog2, unsigned long long* stats) {
   const BatchWork<D, DR> w{items, nitems, gidx, n_dev ? (int64_t)*n_dev : total, clog2};
   find_f64_loop<N, D, DR>(w, B, stats);
+}
+
+// Group mode (see find_f64_loop) over one mesh's points or a batch's, for
+// the points a mixed launch hands over.
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
+    k_find_f64_group(const __grid_constant__ DevMesh m, const BasisTab B, const double* __restrict__ pts,
+                     const int* __restrict__ pidx, int64_t n, const int* __restrict__ n_dev,
+                     int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
+                     double* __restrict__ dist2, unsigned long long* stats) {
+  const SingleWork<D, DR> w{&m, pts, pidx, n_dev ? (int64_t)*n_dev : n, code, elem, rout, dist2, 5};
+  find_f64_loop<N, D, DR, SingleWork<D, DR>, true>(w, B, stats);
+}
+
+template <int N, int D, int DR>
+__global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
+    k_find_f64_group_batch(const BatchItem* __restrict__ items, int nitems, int64_t total,
+                           const int* __restrict__ gidx, const int* __restrict__ n_dev, const BasisTab B,
+                           unsigned long long* stats) {
+  const BatchWork<D, DR> w{items, nitems, gidx, n_dev ? (int64_t)*n_dev : total, 5};
+  find_f64_loop<N, D, DR, BatchWork<D, DR>, true>(w, B, stats);
 }
 
 }  // namespace fp

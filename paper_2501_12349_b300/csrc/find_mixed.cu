@@ -402,8 +402,12 @@ int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pi
     constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
     k_find_mixed<N, D, DR><<<persistent_blocks(n, mixed_ctas(N, D, DR)), kFindThreads, 0, st>>>(
         v, m->basis, pts, pidx, n, code, elem, r, dist2, queue, qcount, stats);
-    k_find_f64<N, D, DR><<<follow_blocks(), kFollowThreads, 0, st>>>(
-        v, m->basis, pts, queue, n, qcount, code, elem, r, dist2, kFollowClog2, fallback_stats(stats));
+    if (n <= kGroupMaxPoints)
+      k_find_f64_group<N, D, DR><<<persistent_blocks(n, f64_ctas(N)), kFindThreads, 0, st>>>(
+          v, m->basis, pts, queue, n, qcount, code, elem, r, dist2, fallback_stats(stats));
+    else
+      k_find_f64<N, D, DR><<<follow_blocks(), kFollowThreads, 0, st>>>(
+          v, m->basis, pts, queue, n, qcount, code, elem, r, dist2, kFollowClog2, fallback_stats(stats));
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
   });
 }
@@ -424,8 +428,12 @@ int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N,
     if (precision == FP_MIXED) {
       k_find_mixed_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, order, B, queue,
                                                                      qcount, clog2, stats);
-      k_find_f64_batch<NN, D, DR><<<follow_blocks(), kFollowThreads, 0, st>>>(
-          items, nitems, total, queue, qcount, B, kFollowClog2, fallback_stats(stats));
+      if (total <= kGroupMaxPoints)
+        k_find_f64_group_batch<NN, D, DR><<<persistent_blocks(total, f64_ctas(NN)), kFindThreads, 0, st>>>(
+            items, nitems, total, queue, qcount, B, fallback_stats(stats));
+      else
+        k_find_f64_batch<NN, D, DR><<<follow_blocks(), kFollowThreads, 0, st>>>(
+            items, nitems, total, queue, qcount, B, kFollowClog2, fallback_stats(stats));
     } else {
       k_find_f64_batch<NN, D, DR><<<blocks, kFindThreads, 0, st>>>(items, nitems, total, order, nullptr, B,
                                                                    clog2, stats);
