@@ -422,7 +422,8 @@ def serve_block(fp, W, torch, dev, args):
     gen_s = time.perf_counter() - t0
     h_min = min(w.h for w in ws)
     dt = 0.1 * h_min / np.sqrt(1.01)
-    srv = fp.Server(entries, mem_budget=8 << 30, max_active=64, precision=fp.FP_MIXED)
+    srv = fp.Server(entries, mem_budget=8 << 30, max_active=64, precision=fp.FP_MIXED,
+                    tick_points=args.serve_tick_points)
     rng = np.random.default_rng(5)
     nmax = 10 ** 6
     pool_r = torch.from_numpy(rng.uniform(-0.01, 1.01, (nmax, 3))).pin_memory()
@@ -458,7 +459,8 @@ def serve_block(fp, W, torch, dev, args):
         return lat
 
     res = {"workload": "8 hex meshes p=3..7 NE 1e4-1e5; requests 1e2-1e6 pts, half remap, half particle (4 RK2 steps)",
-           "generate_and_setup_s": gen_s, "precision": "mixed", "dt": dt}
+           "generate_and_setup_s": gen_s, "precision": "mixed", "dt": dt,
+           "tick_points": args.serve_tick_points}
     burst = draw(args.serve_burst)
 
     def serial_f64(reqs):
@@ -566,6 +568,8 @@ def main():
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-burst", type=int, default=200)
+    ap.add_argument("--serve-tick-points", type=int, default=1 << 20,
+                    help="points per server tick (fp_server_opts.tick_points)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
