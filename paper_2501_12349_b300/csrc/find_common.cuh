@@ -508,12 +508,12 @@ __device__ __forceinline__ T newton_step(const T (&G)[D * DR], const T (&dx)[D],
 #pragma unroll
   for (int j = 0; j < DR; ++j)
 #pragma unroll
-    for (int k = 0; k < DR; ++k) {
+    for (int k = j; k < DR; ++k) {  // G^T G is symmetric: the upper triangle, mirrored
       T s = T(0);
 #pragma unroll
       for (int c = 0; c < D; ++c) s += G[c * DR + j] * G[c * DR + k];
-      HGN[j][k] = s;
-      H[j][k] = beta ? s - HS[j][k] : s;
+      HGN[j][k] = HGN[k][j] = s;
+      H[j][k] = H[k][j] = beta ? s - HS[j][k] : s;
     }
   used_beta = beta;
   bool ok = masked_solve<DR, T>(H, held, g, step);
