@@ -22,7 +22,8 @@
 //     closest BORDER candidate, needing FP64 distances), a refinement that
 //     leaves the element, an ill-conditioned Jacobian, an FP32 iteration at
 //     its rounding floor near a face — goes to a queue in scratch memory, and
-//     k_find_f64 then runs the full FP64 path on the queued points.
+//     the FP64 kernel then runs the full FP64 path on the queued points (in
+//     group mode up to kGroupMaxPoints points per launch, see find_f64.cuh).
 // Points with no candidate are NOT_FOUND straight away.
 #include "find_f64.cuh"
 
