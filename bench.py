@@ -40,7 +40,7 @@ WORKLOAD = "hex3d_32^3_p4_kershaw0.3_1e6pts"
 # DRAM bytes (read + write) of one k_find_f64 launch on the 32^3 p=4 mesh with
 # 10^6 points, from one ncu capture of the current kernel (the summary under
 # profiles/ gives the command); None once the kernel changes.
-F64_TRAFFIC = 595.6e6
+F64_TRAFFIC = 866.5e6
 
 
 def flop_terms(N, d, dr):

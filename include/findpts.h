@@ -75,13 +75,13 @@ extern "C" {
  * counting sort on the device, for calls of at least 16384 points), so the
  * points a warp handles share candidate elements; the paper's remark on the
  * CPU implementation (Sec. 3.2) that processing the points of an element
- * together improves locality.  The cells' points come in two cost classes
- * (2 or more candidate boxes first, then fewer), so the end of a launch,
- * where lanes wait for the slowest point of their warp, runs cheap points.
- * FP_ORDER_GIVEN takes the points as given.  The outputs are identical
- * either way; only the speed differs.  The cell order needs 8 bytes per
- * point plus 16 bytes per cell of scratch, taken from the stream-ordered
- * allocator for the duration of the call. */
+ * together improves locality.  The cells' points come in four cost classes
+ * (3 or more candidate boxes, 2, 1, none), the costly ones first, so the end
+ * of a launch, where lanes wait for the slowest point of their warp, runs
+ * cheap points.  FP_ORDER_GIVEN takes the points as given.  The outputs are
+ * identical either way; only the speed differs.  The cell order needs 8
+ * bytes per point plus 32 bytes per cell of scratch, taken from the
+ * stream-ordered allocator for the duration of the call. */
 #define FP_ORDER_GIVEN 0
 #define FP_ORDER_CELL 1
 

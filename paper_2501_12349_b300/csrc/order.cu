@@ -21,18 +21,14 @@ namespace fp {
 
 namespace {
 
+constexpr int kCostClasses = 4;  // candidates 3+, 2, 1, 0
+
 // Bucket of a point: its cost class, then its cell.  The class counts the
 // candidate elements whose boxes may hold the point (the FP32 box test,
-// undecided cases counted): points with 2 or more come first.  Every
-// candidate but the last costs a whole Newton run, so these are the slow
-// points, and taking them first leaves cheaper ones for the end of the
-// launch, where lanes that run out of points wait for the slowest of their
-// warp.  Each class is one sweep over the mesh in cell order, so the element
-// data is read about once per class: two classes keep the tail as short as
-// four (3+, 2, 1, 0 candidates) with a third less DRAM traffic.
-constexpr int kCostClasses = 2;
-constexpr int kManyCandidates = 2;
-__device__ __forceinline__ int cost_class(int cand) { return cand >= kManyCandidates ? 0 : 1; }
+// undecided cases counted), 3 or more first: every candidate but the last
+// costs a Newton run, so points with many candidates are the slow ones, and
+// taking them first leaves cheap points for the end of the launch, where
+// lanes that run out of points wait for the slowest of their warp.
 template <int D>
 __global__ void __launch_bounds__(256)
     k_point_cells(const __grid_constant__ DevMesh m, int64_t ncell, const double* __restrict__ pts, int64_t n,
@@ -52,9 +48,9 @@ __global__ void __launch_bounds__(256)
     } else {
       int cand = 0;
       const int q0 = __ldg(m.cell_start + cell), q1 = __ldg(m.cell_start + cell + 1);
-      for (int q = q0; q < q1 && cand < kManyCandidates; ++q)
+      for (int q = q0; q < q1 && cand < kCostClasses - 1; ++q)
         cand += boxes_f32<D>(m.box32 + (int64_t)__ldg(m.cell_elems + q) * BOX32, x32) != 0;
-      k = (int)(cost_class(cand) * (ncell + 1) + cell);
+      k = (int)((kCostClasses - 1 - cand) * (ncell + 1) + cell);
     }
     cellof[i] = k;
     atomicAdd(counts + k, 1);
@@ -98,10 +94,10 @@ __global__ void __launch_bounds__(256)
     int cand = 0;
     if (cell >= 0) {  // the cost class, as in k_point_cells
       const int q0 = __ldg(it.m.cell_start + cell), q1 = __ldg(it.m.cell_start + cell + 1);
-      for (int q = q0; q < q1 && cand < kManyCandidates; ++q)
+      for (int q = q0; q < q1 && cand < kCostClasses - 1; ++q)
         cand += boxes_f32<D>(it.m.box32 + (int64_t)__ldg(it.m.cell_elems + q) * BOX32, x32) != 0;
     }
-    const int k = (int)(cost_class(cand) * buckets + it.cell_base + (cell < 0 ? ncell : cell));
+    const int k = (int)((kCostClasses - 1 - cand) * buckets + it.cell_base + (cell < 0 ? ncell : cell));
     key[g] = k;
     atomicAdd(counts + k, 1);
   }
