@@ -12,15 +12,19 @@
 // points) of the current stage of the ready requests, those with the least
 // work left in their stage first, up to a budget of points per tick, so a
 // large request proceeds tile by tile while small ones pass it; it packs the
-// tiles into batch tables grouped by element shape and issues, on one of two
-// tick streams, one find launch per shape (FP64 or mixed), one eval launch
-// per shape and one particle-advance launch; up to two ticks are in flight,
-// and a request's stage ends when all its tiles have finished.  Requests are
-// admitted when a first-fit arena inside a fixed device-memory budget and a
-// slot are free; host<->device copies run on an upload and a download
-// stream of their own, so arriving requests' uploads and finished requests'
-// downloads overlap the ticks and each other (the link's two directions).  Every device wait on the host is bounded (poll + sleep with a
-// deadline); a tick that exceeds it fails its requests with FP_ETIMEDOUT.
+// tiles into batch tables grouped by element shape and issues one find launch
+// per shape (FP64 or mixed) and one eval launch per shape, the shapes side by
+// side on streams forked from the tick's stream (a small shape's launch is
+// bound by its slowest points, not by the GPU, so shapes in sequence would
+// add up their critical paths), then one particle-advance launch; up to two
+// ticks are in flight, and a request's stage ends when all its tiles have
+// finished.  Requests are admitted when a first-fit arena inside a fixed
+// device-memory budget and a slot are free; host<->device copies run on an
+// upload and a download stream of their own, so arriving requests' uploads
+// and finished requests' downloads overlap the ticks and each other (the
+// link's two directions).  Every device wait on the host is bounded (poll +
+// sleep with a deadline); a tick that exceeds it fails its requests with
+// FP_ETIMEDOUT.
 #include <stdlib.h>
 #include <string.h>
 
@@ -200,6 +204,8 @@ struct Tile {
   int64_t id, off, len;
 };
 
+constexpr int kTickForks = 6;
+
 struct TickSlot {
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
@@ -214,8 +220,14 @@ struct TickSlot {
   AdvItem* adv_d = nullptr;
   int* queue = nullptr;
   int64_t queue_cap = 0;
-  int* order = nullptr;  // cell-order scratch of one shape's tiles
+  int* order = nullptr;  // cell-order scratch, carved into one range per shape
   int64_t order_cap = 0;
+  // the shapes of a tick run side by side on these streams, forked from st
+  // after the item tables are uploaded and joined back before the particle
+  // advance and the tick's completion event
+  cudaStream_t fork[kTickForks] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kTickForks] = {};
 };
 
 }  // namespace
@@ -457,28 +469,60 @@ int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& lau
                  int64_t atotal) {
   FP_CUDA_TRY(cudaMemcpyAsync(t.items_d, t.items_h, sizeof(BatchItem) * ni, cudaMemcpyHostToDevice, t.st));
   if (na) FP_CUDA_TRY(cudaMemcpyAsync(t.adv_d, t.adv_h, sizeof(AdvItem) * na, cudaMemcpyHostToDevice, t.st));
-  for (auto& L : launches) {
+  FP_CUDA_TRY(cudaEventRecord(t.fork_ev, t.st));
+  int rc = FP_OK;
+  bool used[kTickForks] = {};
+  int64_t ooff = 0;  // next free int of the cell-order scratch
+  for (size_t li = 0; li < launches.size() && rc == FP_OK; ++li) {
+    const TickLaunch& L = launches[li];
     const int first = std::get<0>(L), cnt = std::get<1>(L);
     const int64_t total = std::get<2>(L), off = std::get<3>(L);
     const int N = std::get<0>(std::get<4>(L)), d = std::get<1>(std::get<4>(L)), dr = std::get<2>(std::get<4>(L));
     const fp_mesh_s* m0 = std::get<5>(L);
     const int64_t buckets = std::get<6>(L);
-    int* qq = t.queue + off;
-    if (s->opts.precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qq + total, 0, sizeof(int), t.st));
-    // the shapes run one after another on t.st, so they share the scratch
-    int* order = nullptr;
-    if (total >= (1 << 14) && batch_cell_order_ints(total, buckets) <= t.order_cap)
-      FP_TRY(batch_cell_order(t.items_d + first, cnt, total, d, buckets, t.order, &order, t.st));
-    FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision,
-                              0, 5, order, qq, qq + total, nullptr, t.st));
-    FP_TRY(dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
-      constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
-      (void)Dc;
-      k_serve_eval<NN, DR><<<grid_for(total, 128, sm_count() * 16), 128, 0, t.st>>>(t.items_d + first, cnt, total,
-                                                                                   m0->basis);
-      return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
-    }));
+    const int f = (int)(li % kTickForks);
+    cudaStream_t fs = t.fork[f];
+    if (!used[f]) {
+      if (cudaStreamWaitEvent(fs, t.fork_ev, 0) != cudaSuccess) {
+        rc = FP_ELAUNCH;
+        break;
+      }
+      used[f] = true;
+    }
+    rc = [&]() -> int {
+      int* qq = t.queue + off;
+      if (s->opts.precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(qq + total, 0, sizeof(int), fs));
+      // each shape has its own range of the order scratch (ranges 64-int aligned)
+      int* order = nullptr;
+      const int64_t need = (batch_cell_order_ints(total, buckets) + 63) / 64 * 64;
+      if (total >= (1 << 14) && ooff + need <= t.order_cap) {
+        FP_TRY(batch_cell_order(t.items_d + first, cnt, total, d, buckets, t.order + ooff, &order, fs));
+        ooff += need;
+      }
+      FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision, 0, 5,
+                                order, qq, qq + total, nullptr, fs));
+      return dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+        constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
+        (void)Dc;
+        k_serve_eval<NN, DR><<<grid_for(total, 128, sm_count() * 16), 128, 0, fs>>>(t.items_d + first, cnt, total,
+                                                                                  m0->basis);
+        return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+      });
+    }();
   }
+  // join every fork that took work, whatever happened, so the tick's event
+  // (recorded on st by the caller) covers all of its kernels
+  for (int f = 0; f < kTickForks; ++f) {
+    if (!used[f]) continue;
+    if (cudaEventRecord(t.join_ev[f], t.fork[f]) != cudaSuccess ||
+        cudaStreamWaitEvent(t.st, t.join_ev[f], 0) != cudaSuccess) {
+      // the join failed: wait for the fork on the host so that no kernel
+      // outlives the tick
+      cudaStreamSynchronize(t.fork[f]);
+      if (rc == FP_OK) rc = FP_ELAUNCH;
+    }
+  }
+  if (rc != FP_OK) return rc;
   if (na) {
     k_advance<<<grid_for(atotal, 256, sm_count() * 8), 256, 0, t.st>>>(t.adv_d, na, atotal);
     FP_CUDA_TRY(cudaGetLastError());
@@ -587,6 +631,11 @@ void destroy_server(fp_server_s* s) {
   for (auto& t : s->slot) {
     if (t.st) cudaStreamDestroy(t.st);
     if (t.done) cudaEventDestroy(t.done);
+    for (int f = 0; f < kTickForks; ++f) {
+      if (t.fork[f]) cudaStreamDestroy(t.fork[f]);
+      if (t.join_ev[f]) cudaEventDestroy(t.join_ev[f]);
+    }
+    if (t.fork_ev) cudaEventDestroy(t.fork_ev);
     cudaFreeHost(t.items_h);
     cudaFreeHost(t.adv_h);
     cudaFree(t.items_d);
@@ -643,7 +692,10 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
   const int64_t qcap = (int64_t)(o.mem_budget / 72) + 2 * 64 + 16;
   int64_t all_buckets = 0;
   for (auto& me : s->meshes) all_buckets += me.m->ncell + 1;
-  const int64_t ocap = batch_cell_order_ints(std::min(qcap, o.tick_points), all_buckets);
+  // one order range per shape: the single-range size plus, per shape, its
+  // own scan's constant part and the 64-int alignment
+  const int64_t ocap = batch_cell_order_ints(std::min(qcap, o.tick_points), all_buckets) +
+                       (int64_t)(s->meshes.size() + 1) * 256;
   int rc = FP_OK;
   if (!s->arena.init(o.mem_budget)) rc = FP_ENOMEM;
   if (rc == FP_OK && (cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking) != cudaSuccess ||
@@ -653,7 +705,11 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
     if (rc != FP_OK) break;
     t.queue_cap = qcap;
     t.order_cap = ocap;
-    if (cudaStreamCreateWithFlags(&t.st, cudaStreamNonBlocking) != cudaSuccess ||
+    bool forks_ok = cudaEventCreateWithFlags(&t.fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int f = 0; f < kTickForks && forks_ok; ++f)
+      forks_ok = cudaStreamCreateWithFlags(&t.fork[f], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&t.join_ev[f], cudaEventDisableTiming) == cudaSuccess;
+    if (!forks_ok || cudaStreamCreateWithFlags(&t.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&t.items_h, sizeof(BatchItem) * s->max_items) != cudaSuccess ||
         cudaMallocHost(&t.adv_h, sizeof(AdvItem) * s->max_items) != cudaSuccess)
