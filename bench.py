@@ -568,7 +568,7 @@ def main():
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-burst", type=int, default=200)
-    ap.add_argument("--serve-tick-points", type=int, default=1 << 20,
+    ap.add_argument("--serve-tick-points", type=int, default=1 << 19,
                     help="points per server tick (fp_server_opts.tick_points)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

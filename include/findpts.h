@@ -297,8 +297,10 @@ typedef struct {
   int precision;         /* FP_F64 or FP_MIXED                                 */
   double tick_timeout_s; /* host watchdog per tick: its requests fail with     */
                          /* FP_ETIMEDOUT (memory kept until the tick ends)     */
-  int64_t tick_points;   /* points per tick: a request's stage is split into   */
-                         /* tiles, the requests with the least work left first */
+  int64_t tick_points;   /* points per tick (default 2^19): a request's stage  */
+                         /* is split into tiles, the requests with the least   */
+                         /* work left first; fewer points per tick lower the   */
+                         /* latency of small requests and cost capacity        */
 } fp_server_opts;
 
 typedef struct {
@@ -307,7 +309,7 @@ typedef struct {
   size_t bytes_in_use;
 } fp_server_stats;
 
-void fp_server_opts_default(fp_server_opts* opts); /* 1 GiB, 64 slots, FP_MIXED, 30 s, 2^20 */
+void fp_server_opts_default(fp_server_opts* opts); /* 1 GiB, 64 slots, FP_MIXED, 30 s, 2^19 */
 
 /* remap_fields[i] ([nc_remap[i]][NE][N^dr], device) and velocity[i]
  * ([d][NE][N^dr], device) may be NULL (arrays themselves may be NULL); they

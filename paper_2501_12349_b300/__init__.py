@@ -397,7 +397,7 @@ class Server:
     with fields as device tensors [nc][NE][N^dr]."""
 
     def __init__(self, entries, mem_budget: int = 1 << 30, max_active: int = 64, precision: int = FP_MIXED,
-                 tick_timeout_s: float = 30.0, tick_points: int = 1 << 20):
+                 tick_timeout_s: float = 30.0, tick_points: int = 1 << 19):
         L = _server_sig()
         o = fp_server_opts_default()
         o.mem_budget, o.max_active, o.precision, o.tick_timeout_s = mem_budget, max_active, precision, tick_timeout_s

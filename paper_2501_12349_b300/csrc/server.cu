@@ -659,7 +659,7 @@ extern "C" void fp_server_opts_default(fp_server_opts* o) {
   o->max_active = 64;
   o->precision = FP_MIXED;
   o->tick_timeout_s = 30.0;
-  o->tick_points = (int64_t)1 << 20;
+  o->tick_points = (int64_t)1 << 19;
 }
 
 extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* const* remap_fields,
