@@ -92,13 +92,16 @@ def test_particles_match_reference(fp, torch, resident):
     s.close()
 
 
-def test_same_alone_and_in_mix(fp, torch, resident):
-    """A request's results do not depend on what else is in flight."""
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_same_alone_and_in_mix(fp, torch, resident, precision):
+    """A request's results do not depend on what else is in flight: the
+    meshes' element shapes of one tick run side by side on forked streams,
+    in either precision."""
     rng = np.random.default_rng(53)
     pa = rng.uniform(-0.02, 1.02, (3000, 3))
     pp = rng.uniform(0.05, 0.95, (2000, 3))
     dt = 0.02
-    s = server_of(fp, resident)
+    s = server_of(fp, resident, precision=fp.FP_MIXED if precision == "mixed" else fp.FP_F64)
     alone_a = [a.copy() for a in s.wait(s.submit(2, fp.FP_REQ_REMAP, pa))]
     alone_p = [a.copy() for a in s.wait(s.submit(0, fp.FP_REQ_PARTICLE, pp, rk_steps=3, dt=dt))]
     ids = []
