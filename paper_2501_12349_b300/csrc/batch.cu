@@ -72,7 +72,7 @@ int launch_eval_class(const BatchItem* items, int nitems, int64_t total, int N, 
 }
 
 struct Tuning {
-  int ctas_per_sm = 0;  // 0: the kernel's own (3 mixed; f64_ctas(N) FP64)
+  int ctas_per_sm = 0;  // 0: the kernel's own (mixed_ctas(N, d, dr) mixed; f64_ctas(N) FP64)
   int clog2 = 5;
   float ms = -1.f;  // measured time of the chosen shape, -1 if untuned
 };
