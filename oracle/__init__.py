@@ -67,6 +67,7 @@ def lib():
             "or_box_candidates": [_int, _i64, _D, _D, _D, _D, _i64, _I32, _I32],
             "or_eval": [_D, _int, _int, _int, _i64, _I32, _I32, _D, _i64, _D],
             "or_forward_map": [_D, _int, _int, _int, _i64, _I32, _D, _i64, _D, _D],
+            "or_surface_frame": [_D, _D, _D],
             "or_num_threads": [],
         }
         for name, args in sig.items():
@@ -156,6 +157,15 @@ def bound_2d(u, M: int):
     lo, hi = _dbl(), _dbl()
     assert lib().or_bound_2d(N, M, _p(u), ctypes.byref(lo), ctypes.byref(hi)) == 0
     return lo.value, hi.value
+
+
+def surface_frame(Jc):
+    """Sec. 4.2 frame of a surface quad from its 3x2 Jacobian at r = 0:
+    returns (R1, R) with R1 the Rodrigues rotation and R = R2 R1."""
+    Jc = _f64(Jc).reshape(3, 2)
+    R1, R = np.zeros((3, 3)), np.zeros((3, 3))
+    assert lib().or_surface_frame(_p(Jc), _p(R1), _p(R)) == 0
+    return R1, R
 
 
 def element_boxes(coords, d: int, dr: int, N: int, tol: float = 0.1, M: int = 0):

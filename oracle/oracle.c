@@ -449,7 +449,7 @@ static void expand_box(int d, const double* lo, const double* hi, double tol, do
 /* Orientation frame of a surface quad, Sec. 4.2: with t1, t2 the tangents at
  * r = 0 and n = t1 x t2, R1 is the Rodrigues rotation taking n/|n| to the z
  * axis and R2 = [R1 t1, R1 t2, e3]^{-1} (columns); the frame is R = R2 R1.   */
-static void surface_frame(const double* Jc /* 3x2 */, double* R) {
+static void surface_frame(const double* Jc /* 3x2 */, double* R1out, double* R) {
   double t1[3] = {Jc[0], Jc[2], Jc[4]}, t2[3] = {Jc[1], Jc[3], Jc[5]};
   double n[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
                  t1[0] * t2[1] - t1[1] * t2[0]};
@@ -481,6 +481,8 @@ static void surface_frame(const double* Jc /* 3x2 */, double* R) {
     a[i] = R1[i * 3 + 0] * t1[0] + R1[i * 3 + 1] * t1[1] + R1[i * 3 + 2] * t1[2];
     b[i] = R1[i * 3 + 0] * t2[0] + R1[i * 3 + 1] * t2[1] + R1[i * 3 + 2] * t2[2];
   }
+  if (R1out)
+    for (int i = 0; i < 9; ++i) R1out[i] = R1[i];
   double Mc[9] = {a[0], b[0], 0.0, a[1], b[1], 0.0, a[2], b[2], 1.0}, R2[9];
   inv_small(3, Mc, R2);
   for (int i = 0; i < 3; ++i)
@@ -530,6 +532,14 @@ static void line_frame(int d, const double* t, double* R) {
   for (int i = 0; i < 9; ++i) R[i] = ((i % 4) == 0 ? 1.0 : 0.0) + s * K[i] + (1.0 - co) * K2[i];
 }
 
+/* The surface frame of Sec. 4.2 for a 3x2 Jacobian J_c at r = 0 (row-major,
+ * J_c[c][j] = dx_c/dr_j): R1 (the Rodrigues rotation) and R = R2 R1, both
+ * 3x3 row-major.  Exported for the tests; element boxes use the same call. */
+int or_surface_frame(const double* Jc, double* R1, double* R) {
+  surface_frame(Jc, R1, R);
+  return 0;
+}
+
 /* Secs. 3.1.1-3.1.2 and 4.1-4.2: the expanded AABB and OBB of every element.
  * AABB: bounds of each coordinate function (element_bounds), expanded.
  * OBB: x_c = x(r=0), J_c = G(r=0); the nodes are mapped to the frame
@@ -570,7 +580,7 @@ int or_element_boxes(const double* coords, int d, int dr, int N, int64_t NE, dou
         err = 1;
       }
     } else if (dr == 2) {
-      surface_frame(Jc, T);
+      surface_frame(Jc, NULL, T);
     } else {
       line_frame(d, Jc, T); /* Jc is the d x 1 tangent */
     }

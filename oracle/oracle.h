@@ -52,6 +52,7 @@ int or_eval(const double* field, int nc, int dr, int N, int64_t NE, const int32_
             const int32_t* elem, const double* r, int64_t n, double* out);
 int or_forward_map(const double* coords, int d, int dr, int N, int64_t NE,
                    const int32_t* elem, const double* r, int64_t n, double* x, double* jac);
+int or_surface_frame(const double* Jc, double* R1, double* R);
 int or_num_threads(void);
 void or_set_num_threads(int n);
 

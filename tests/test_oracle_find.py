@@ -462,3 +462,96 @@ def test_line_forward_map_recovered(name):
     assert np.all(code == 0)
     np.testing.assert_array_equal(elem, el)
     np.testing.assert_allclose(r, rt, atol=1e-12)
+
+
+def numpy_jacobian(coords, d, dr, N, e, r):
+    """Independent dx_c/dr_j of x_e (Eq. jacobian) at one r, with numpy
+    Legendre fits of the 1D Lagrange bases and their derivatives."""
+    z = W.gll_points(N)
+    ne = N ** dr
+    fits = [L.legfit(z, np.eye(N)[i], N - 1) for i in range(N)]
+    V = [np.array([L.legval(r[j], f) for f in fits]) for j in range(dr)]
+    D = [np.array([L.legval(r[j], L.legder(f)) for f in fits]) for j in range(dr)]
+    idx = np.arange(ne)
+    J = np.zeros((d, dr))
+    for j in range(dr):
+        w = np.ones(ne)
+        for k in range(dr):
+            w = w * (D[k] if k == j else V[k])[(idx // N ** k) % N]
+        J[:, j] = [coords[c, e] @ w for c in range(d)]
+    return J
+
+
+def _frame_checks(J):
+    """Sec. 4.2 on one 3x2 Jacobian: R1 is a proper rotation taking the unit
+    normal n = t1 x t2 / |t1 x t2| to e3, and R = R2 R1 takes t1, t2, n to
+    e1, e2, e3 (R2 is the inverse of [R1 t1, R1 t2, e3])."""
+    t1, t2 = J[:, 0], J[:, 1]
+    n = np.cross(t1, t2)
+    n /= np.linalg.norm(n)
+    R1, R = oracle.surface_frame(J)
+    np.testing.assert_allclose(R1 @ R1.T, np.eye(3), atol=1e-14)
+    assert abs(np.linalg.det(R1) - 1.0) < 1e-14
+    np.testing.assert_allclose(R1 @ n, [0.0, 0.0, 1.0], atol=1e-14)
+    np.testing.assert_allclose(R @ np.column_stack([t1, t2, n]), np.eye(3), atol=1e-13)
+    return R, n
+
+
+@pytest.mark.parametrize("name", ["sphere", "torus"])
+def test_surface_frame_is_sec42(name):
+    """The surface OBB frame (Sec. 4.2) of every element of the sphere and
+    torus meshes: the checks of _frame_checks on J_c = G(0) computed
+    independently with numpy, and the stored OBB matrix A = diag(1/hw) R
+    (Eq. OBB_test) maps t1, t2, n onto positive multiples of e1, e2, e3."""
+    coords, d, dr, N = MESHES[name]()
+    m = oracle.OracleMesh(coords, d, dr, N)
+    for e in range(m.NE):
+        J = numpy_jacobian(m.coords, 3, 2, N, e, np.zeros(2))
+        _, n = _frame_checks(J)
+        M = m.obb_A[e] @ np.column_stack([J[:, 0], J[:, 1], n])
+        diag = np.diag(M)
+        assert np.all(diag > 0), (name, e)
+        off = M - np.diag(diag)
+        assert np.max(np.abs(off)) <= 1e-12 * np.max(diag), (name, e)
+
+
+def test_surface_frame_special_orientations():
+    """Frames for tangents whose normal is +e3, -e3 (the rotation's axis is
+    undefined there), nearly -e3, and random orientations and shears."""
+    rng = np.random.default_rng(42)
+    cases = [np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 0.0]]),        # n = +e3
+             np.array([[0.0, 1.0], [1.0, 0.0], [0.0, 0.0]]),        # n = -e3
+             np.array([[0.0, 1.0], [1.0, 0.0], [1e-9, 0.0]]),       # n close to -e3
+             np.array([[0.2, 0.0], [0.0, -3.0], [0.0, 0.0]])]       # scaled, n = -e3
+    for _ in range(40):
+        cases.append(rng.normal(size=(3, 2)) * rng.uniform(0.01, 10.0))
+    for J in cases:
+        _frame_checks(J)
+
+
+@pytest.mark.parametrize("N", [2, 4, 6])
+def test_surface_obb_affine_closed_form(N):
+    """A flat parallelogram quad x = x_c + t1 r + t2 s in 3D (any
+    orientation): in the frame R of Sec. 4.2 its nodes are (r, s, 0), so the
+    expanded frame box has half-widths (1+tol)(1, 1) and, for the zero
+    normal extent (Sec. 4.1), tol * Lmin / 2 = tol with Lmin = 2: the stored
+    A is diag(1/1.1, 1/1.1, 1/0.1) [t1 t2 n]^{-1} and the OBB centre is x_c."""
+    rng = np.random.default_rng(7 + N)
+    z = W.gll_points(N)
+    rr, ss = np.meshgrid(z, z, indexing="xy")  # node i + N j: r fastest
+    rr, ss = rr.reshape(-1), ss.reshape(-1)
+    elems, frames = [], []
+    for _ in range(6):
+        t1, t2 = rng.normal(size=3), rng.normal(size=3)
+        xc = rng.uniform(-2, 2, 3)
+        x = xc[:, None] + t1[:, None] * rr[None] + t2[:, None] * ss[None]
+        elems.append(x)
+        n = np.cross(t1, t2)
+        n /= np.linalg.norm(n)
+        frames.append((xc, np.column_stack([t1, t2, n])))
+    coords = np.ascontiguousarray(np.stack(elems, axis=1))  # [3][NE][N^2]
+    m = oracle.OracleMesh(coords, 3, 2, N)
+    for e, (xc, B) in enumerate(frames):
+        A = np.diag([1 / 1.1, 1 / 1.1, 1 / 0.1]) @ np.linalg.inv(B)
+        np.testing.assert_allclose(m.obb_A[e], A, rtol=1e-11, atol=1e-11 * np.abs(A).max())
+        np.testing.assert_allclose(m.obb_c[e], xc, atol=1e-12 * (1 + np.abs(xc).max()))
