@@ -37,10 +37,67 @@ METRIC = "located+evaluated points/s (3D hex p=4)"
 WORKLOAD = "hex3d_32^3_p4_kershaw0.3_1e6pts"
 
 
-# DRAM bytes (read + write) of one k_find_f64 launch on the 32^3 p=4 mesh with
-# 10^6 points, from one ncu capture of the current kernel (the summary under
-# profiles/ gives the command); None once the kernel changes.
-F64_TRAFFIC = 866.5e6
+# DRAM bytes (read + write) per launch of a kernel on this workload (32^3
+# p=4 mesh, 10^6 points), from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), with the SHA-256 of the kernel's source files at
+# the time of the capture: the figure is reported only while the sources
+# are unchanged, and as null once they differ.
+PKG_SRC = ROOT / "paper_2501_12349_b300" / "csrc"
+KERNEL_SOURCES = {
+    "k_find_f64": ["find_f64.cuh", "find_common.cuh", "fp_basis.cuh", "beta_warp.cuh", "fp_common.cuh",
+                   "find.cu", "order.cu"],
+    "k_find_mixed": ["find_mixed.cu", "find_f64.cuh", "find_common.cuh", "fp_basis.cuh", "beta_warp.cuh",
+                     "fp_common.cuh", "find.cu", "order.cu"],
+}
+TRAFFIC = {}
+
+
+def source_sha(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(name.encode())
+        h.update((PKG_SRC / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(kernel: str):
+    """(bytes per launch, note): the captured figure while the kernel's
+    sources hash to the value it was captured with, else (None, why)."""
+    rec = TRAFFIC.get(kernel)
+    sha = source_sha(kernel)
+    if rec is None:
+        return None, f"no capture for sources {sha}"
+    if rec["sha"] != sha:
+        return None, f"captured for sources {rec['sha']}, now {sha}"
+    return rec["bytes"], f"ncu capture, sources {sha}"
+
+
+def iteration_model_flops(C, I, N, d):
+    """The per-candidate and per-iteration flop model of a 3D find: per
+    candidate the box tests (~30) and the closest-node start over all
+    n_e = N^3 nodes (3 d n_e), per Newton iteration x and G by sum
+    factorisation (2 (6 N^3 + 9 N^2 + 12 N)), the bases (~30 N) and the step
+    algebra (~60); candidate and iteration counts are the kernel's own
+    counters (they equal the oracle's: same candidates, iterations within
+    1%)."""
+    return float(C * (30 + 3 * d * N ** 3) + I * (2 * (6 * N ** 3 + 9 * N ** 2 + 12 * N) + 30 * N + 60))
+
+
+def boxes_flops(NE, N, M, d, dr):
+    """FP64 flops of k_boxes' function bounds (Secs. 3.1.1-3.1.2): for every
+    bounding piece (6 faces of a hex, 4 edges of a quad, the element of a
+    surface quad or line), coordinate and box kind (AABB, OBB frame), a
+    lower and an upper bound over the M^dp Chebyshev grid points (dp the
+    piece's dimension), each an N^dp-term sum of FMAs (Eq. 2D_function_bound
+    with the min/max of the products precomputed)."""
+    if dr == 3:
+        pieces, dp = 6, 2
+    elif d == 2 and dr == 2:
+        pieces, dp = 4, 1
+    else:
+        pieces, dp = 1, dr
+    return float(NE * pieces * d * 2 * 2 * 2 * (N ** dp) * (M ** dp))
 
 
 def flop_terms(N, d, dr):
@@ -90,8 +147,15 @@ def mixed_flop_model(stats, N, d, dr):
     the residual in FP64; the normal equations and their solve in FP32 for
     volumes, in FP64 with the FP64 Jacobian for surfaces and lines), and the
     FP64 kernel on the handed-over points (counters [8]-[15])."""
+    f32, f64_main, f64_follow = mixed_flop_parts(stats, N, d, dr)
+    return f32, f64_main + f64_follow
+
+
+def mixed_flop_parts(stats, N, d, dr):
+    """(FP32 flops of k_find_mixed, FP64 flops of k_find_mixed (its
+    refinements), FP64 flops of the FP64 kernel on the handed-over points)."""
     t = flop_terms(N, d, dr)
-    C, R = int(stats[0]), int(stats[4])
+    R = int(stats[4])
     f32 = find_flops(stats[0:8], N, d, dr, "linear")
     refine = d * (t["eval_x"] - t["basis"]) + t["basis"] + 2 * d
     solve = 2 * d * dr * (dr + 1) + 30
@@ -99,8 +163,7 @@ def mixed_flop_model(stats, N, d, dr):
         f32 += R * solve
     else:
         refine += solve
-    f64 = R * refine + find_flops(stats[8:16], N, d, dr, "node")
-    return float(f32), float(f64)
+    return float(f32), float(R * refine), float(find_flops(stats[8:16], N, d, dr, "node"))
 
 
 class ClockSampler:
@@ -254,6 +317,8 @@ def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, peaks):
             fp.fp_findpts(mesh.handle, pts, code, elem, r, d2)
             fp.fp_eval(mesh.handle, code, elem, r, field, 3, out)
         fms, ems = [], []
+        fp.fp_kernel_times(mesh.handle)
+        fp.fp_set_timing(mesh.handle, True)
         for _ in range(steps):
             flush.zero_()
             a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -265,6 +330,9 @@ def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, peaks):
             c.synchronize()
             fms.append(a.elapsed_time(b))
             ems.append(b.elapsed_time(c))
+        fp.fp_set_timing(mesh.handle, False)
+        kms, kcalls = fp.fp_kernel_times(mesh.handle)
+        kavg = [kms[i] / max(kcalls[i], 1) / 1e3 for i in range(fp.FP_NTIMES)]
         t = (sum(fms) + sum(ems)) / 1e3
         if world > 1:
             tt = torch.tensor([t], device=dev)
@@ -275,12 +343,26 @@ def mixed_block(fp, W, torch, dev, st, flush, args, rank, world, dist, peaks):
         sv = stats.cpu().numpy()
         outs[prec] = (code.clone(), elem.clone(), r.clone())
         fsec = statistics.mean(fms) / 1e3
+        kernels = {}
         if prec == "f64":
             f32, f64 = 0.0, find_flops(sv, w.N, 3, 3, "node")
+            model = iteration_model_flops(sv[0], sv[1], w.N, 3)
+            kernels["k_find_f64"] = {"ms": kavg[fp.FP_TIME_FIND] * 1e3,
+                                     "fp64_frac": model / kavg[fp.FP_TIME_FIND] / 1e12 / peaks[0],
+                                     "fp64_frac_counted_work": f64 / kavg[fp.FP_TIME_FIND] / 1e12 / peaks[0]}
         else:
             f32, f64 = mixed_flop_model(sv, w.N, 3, 3)
+            a32, a64m, a64f = mixed_flop_parts(sv, w.N, 3, 3)
+            km, kf = kavg[fp.FP_TIME_FIND], kavg[fp.FP_TIME_FOLLOW]
+            kernels["k_find_mixed"] = {"ms": km * 1e3, "fp32_tflops": a32 / km / 1e12,
+                                       "fp32_frac": a32 / km / 1e12 / peaks[1],
+                                       "fp64_tflops": a64m / km / 1e12, "fp64_frac": a64m / km / 1e12 / peaks[0]}
+            kernels["fp64_follow_up"] = {"ms": kf * 1e3, "fp64_tflops": a64f / max(kf, 1e-9) / 1e12,
+                                         "fp64_frac": a64f / max(kf, 1e-9) / 1e12 / peaks[0]}
+        kernels["cell_order_ms"] = kavg[fp.FP_TIME_ORDER] * 1e3
+        kernels["k_eval_f64_ms"] = kavg[fp.FP_TIME_EVAL] * 1e3
         res[prec] = {"value": world * n * steps / t, "unit": "points/s",
-                     "find_ms": statistics.mean(fms), "eval_ms": statistics.mean(ems),
+                     "find_ms": statistics.mean(fms), "eval_ms": statistics.mean(ems), "kernels": kernels,
                      "pipes": {"fp64": {"achieved": f64 / fsec / 1e12, "frac": f64 / fsec / 1e12 / peaks[0]},
                                "fp32": {"achieved": f32 / fsec / 1e12, "frac": f32 / fsec / 1e12 / peaks[1]},
                                "unit": "TFLOP/s", "time": "whole find call (all its kernels)"},
@@ -542,9 +624,18 @@ def serve_block(fp, W, torch, dev, args):
             ids.append(submit(q))
         lat = collect(ids)
         wall = time.perf_counter() - t0
+        sizes = np.array([q[2] for q in reqs])
+        lat_a = np.array(lat)
+        by_size = []
+        for lo, hi in ((1e2, 1e3), (1e3, 1e4), (1e4, 1e5), (1e5, 1e6 + 1)):
+            sel = (sizes >= lo) & (sizes < hi)
+            if sel.any():
+                by_size.append({"points": f"[{lo:.0e}, {min(hi, 1e6):.0e})", "requests": int(sel.sum()),
+                                "p50_ms": 1e3 * float(np.percentile(lat_a[sel], 50)),
+                                "p99_ms": 1e3 * float(np.percentile(lat_a[sel], 99))})
         res["load"].append({"rho": rho, "arrival_rate_rps": lam, "requests": len(reqs), "wall_s": wall,
                             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                            "mean_ms": 1e3 * float(np.mean(lat)),
+                            "mean_ms": 1e3 * float(np.mean(lat)), "by_size": by_size,
                             "request_points_per_s": sum(q[2] for q in reqs) / wall,
                             "stage_points_per_s": stage_points(reqs) / wall})
     st = srv.stats()
@@ -566,7 +657,7 @@ def main():
     ap.add_argument("--skip-mixed", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-burst", type=int, default=200)
     ap.add_argument("--serve-tick-points", type=int, default=1 << 19,
                     help="points per server tick (fp_server_opts.tick_points)")
@@ -624,6 +715,8 @@ def main():
     time.sleep(0.3)  # nvidia-smi is sampling by now
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    fp.fp_kernel_times(mesh.handle)  # start the per-kernel intervals afresh
+    fp.fp_set_timing(mesh.handle, True)
     barrier()
     torch.cuda.synchronize()
     clocks.mark(True)
@@ -640,6 +733,11 @@ def main():
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
+    fp.fp_set_timing(mesh.handle, False)
+    kms, kcalls = fp.fp_kernel_times(mesh.handle)
+    kernel_ms = {name: kms[i] / max(kcalls[i], 1) for i, name in
+                 ((fp.FP_TIME_ORDER, "cell_order"), (fp.FP_TIME_FIND, "find_kernel"),
+                  (fp.FP_TIME_FOLLOW, "fp64_follow_up"), (fp.FP_TIME_EVAL, "eval")) if kcalls[i]}
     find_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
     eval_ms = [ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)]
     step_ms = [a + b for a, b in zip(find_ms, eval_ms)]
@@ -663,16 +761,37 @@ def main():
     find_avg = statistics.mean(find_ms) / 1e3
     eval_avg = statistics.mean(eval_ms) / 1e3
     peak_src = "FP64 FMA pipe, measured live by fp_alu_peak (no FP64 entry in the measured peaks file)"
+    # the dominant kernel's own average duration (CUDA events recorded by
+    # the library between the kernels of each timed call, on its stream)
+    kfind = kernel_ms.get("find_kernel", statistics.mean(find_ms)) / 1e3
     if args.precision == "f64":
-        ach = fl_find / find_avg / 1e12
+        model = iteration_model_flops(sv[0], sv[1], w.N, 3)
+        ach = model / kfind / 1e12
+        traffic, tnote = traffic_of("k_find_f64")
         roofline = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
-                    "traffic": F64_TRAFFIC, "kernel": "k_find_f64", "peak_source": peak_src}
+                    "traffic": traffic, "traffic_source": tnote, "kernel": "k_find_f64",
+                    "kernel_ms": kfind * 1e3, "peak_source": peak_src,
+                    "flop_model": "per candidate 30 + 3 d N^3, per iteration 2(6N^3+9N^2+12N) + 30N + 60",
+                    "flops_per_launch": model,
+                    "counted_work": {"achieved": fl_find / kfind / 1e12, "frac": fl_find / kfind / 1e12 / peak64,
+                                     "flops_per_launch": fl_find,
+                                     "model": "only the evaluations the kernel performs (node start without a "
+                                              "full evaluation), face-restricted beta term, 60 per step"},
+                    "whole_call": {"ms": find_avg * 1e3, "frac": model / find_avg / 1e12 / peak64}}
     else:
         f32, f64 = mixed_flop_model(sv, w.N, 3, 3)
         a64, a32 = f64 / find_avg / 1e12, f32 / find_avg / 1e12
+        traffic, tnote = traffic_of("k_find_mixed")
         roofline = {"bound": "alu", "achieved": a64, "peak": peak64, "unit": "TFLOP/s", "frac": a64 / peak64,
-                    "traffic": None, "kernel": "k_find_mixed + k_find_f64 (FP64 pipe)", "peak_source": peak_src,
+                    "traffic": traffic, "traffic_source": tnote,
+                    "kernel": "k_find_mixed + k_find_f64 (FP64 pipe)", "peak_source": peak_src,
                     "fp32": {"achieved": a32, "peak": peak32, "frac": a32 / peak32}}
+    info = mesh.info()
+    fb = boxes_flops(w.NE, w.N, info.M, 3, 3)
+    setup_roofline = {"kernel": "k_boxes", "bound": "alu", "ms": info.setup_boxes_ms,
+                      "achieved": fb / (info.setup_boxes_ms / 1e3) / 1e12, "peak": peak64, "unit": "TFLOP/s",
+                      "frac": fb / (info.setup_boxes_ms / 1e3) / 1e12 / peak64, "flops": fb,
+                      "grid_build_ms": info.setup_grid_ms, "setup_call_ms": setup_ms}
 
     # end to end through host buffers: fp_findpts_host, the public call for
     # host data (pinned points in; code, elem, r, dist2 and the interpolated
@@ -722,11 +841,13 @@ def main():
                        "parallelism": f"replicas{world}"},
             # per step: the cell order (k_point_cells; the bucket scan
             # k_scan_tiles, k_scan, k_scan_add; k_point_scatter), the find
-            # (k_find_f64; mixed: k_find_mixed + k_find_f64 on the handed-over
-            # points) and k_eval_f64, as the launch list under profiles/ shows
+            # (k_find_f64; mixed: k_find_mixed + the FP64 kernel on the
+            # handed-over points) and k_eval_f64
             "gpu_launches": (7 if args.precision == "f64" else 8) * args.steps,
             "roofline": roofline,
-            "kernels_ms": {"find": statistics.mean(find_ms), "eval": statistics.mean(eval_ms)},
+            "setup_roofline": setup_roofline,
+            "kernels_ms": {"find_call": statistics.mean(find_ms), "eval_call": statistics.mean(eval_ms),
+                           **kernel_ms},
             "eval_roofline": {"bound": "alu", "achieved": fl_eval / eval_avg / 1e12, "peak": peak64,
                               "unit": "TFLOP/s", "frac": fl_eval / eval_avg / 1e12 / peak64},
             "find_counters": {"candidates": int(sv[0]), "iterations": int(sv[1]), "rejected": int(sv[2]),

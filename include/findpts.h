@@ -164,7 +164,10 @@ int fp_findpts_stats(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
  *   rejected with FP_EINVAL before anything runs; split larger sets.
  *   The first call on a device looks up the array's device address (a
  *   one-time set-up per device, with that device current); make that first
- *   call before any stream capture.
+ *   call before any stream capture.  The address is kept for the rest of
+ *   the process: after a cudaDeviceReset of that device (by any code in the
+ *   process) it is stale, so do not call this entry point on a device that
+ *   has been reset.
  *   All calls share the one array: calls that can overlap on the GPU (on
  *   different streams, or from different threads) race and must be
  *   serialised by the caller.  Each call clears the queue's counter. */
@@ -345,7 +348,12 @@ int fp_server_release(fp_server s, int64_t req_id);
 
 int fp_server_get_stats(fp_server s, fp_server_stats* stats);
 
-/* Stops the scheduler, waits for the device, frees everything. */
+/* Stops the scheduler, waits for the work the server queued on its own
+ * streams (with the tick watchdog limit as deadline; other work on the
+ * device is not waited for) and frees everything.  If that wait runs out,
+ * returns FP_ETIMEDOUT and leaves the server's device and pinned buffers
+ * allocated (leaked), since kernels may still use them; the handle is
+ * invalid either way. */
 int fp_server_destroy(fp_server s);
 
 /* ---- introspection (tests, benchmarks) ----------------------------------- */
@@ -354,7 +362,28 @@ typedef struct {
   int64_t NE, n_cells, n_cell_entries;
   double grid_lo[3], grid_hi[3];
   size_t device_bytes;
+  double setup_boxes_ms; /* k_boxes (Secs. 3.1.1-3.1.2) at setup, CUDA events   */
+  double setup_grid_ms;  /* the Psi_L build (Sec. 3.1.3) at setup, CUDA events  */
 } fp_mesh_info;
+
+/* Per-kernel timing of find and eval calls (the paper has no counterpart;
+ * it serves roofline measurements).  With timing on, every later
+ * fp_findpts / fp_findpts_stats / fp_eval / fp_eval_order call on the mesh
+ * records CUDA events on its stream between its kernels; fp_kernel_times
+ * waits for the recorded events, adds up the intervals per stage since its
+ * last call and starts over.  Stages: */
+#define FP_TIME_ORDER 0  /* the cell order (fp_set_point_order)               */
+#define FP_TIME_FIND 1   /* the find kernel (k_find_f64, or k_find_mixed)     */
+#define FP_TIME_FOLLOW 2 /* FP_MIXED: the FP64 kernel on the handed-over points */
+#define FP_TIME_EVAL 3   /* the interpolation kernel                           */
+#define FP_NTIMES 4
+/* on = 0 stops recording (intervals recorded so far stay readable).
+ * Errors: FP_EINVAL, FP_ENOMEM. */
+int fp_set_timing(fp_mesh m, int on);
+/* ms[FP_NTIMES]: summed milliseconds per stage; calls[FP_NTIMES] (may be
+ * NULL): intervals per stage.  At most 65536 intervals are kept between two
+ * reads; later ones are dropped.  Errors: FP_EINVAL, FP_ELAUNCH. */
+int fp_kernel_times(fp_mesh m, double* ms, int64_t* calls);
 
 /* Host call; fills *info. */
 int fp_get_info(fp_mesh m, fp_mesh_info* info);

@@ -22,6 +22,7 @@ FP_F64, FP_MIXED = 0, 1
 FP_ORDER_GIVEN, FP_ORDER_CELL = 0, 1
 FP_MAX_N = 8
 FP_NSTATS = 16
+FP_TIME_ORDER, FP_TIME_FIND, FP_TIME_FOLLOW, FP_TIME_EVAL, FP_NTIMES = 0, 1, 2, 3, 4
 
 
 class FindptsError(RuntimeError):
@@ -40,7 +41,8 @@ class FpMeshInfo(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("dr", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int),
                 ("n_grid", ctypes.c_int), ("NE", ctypes.c_int64), ("n_cells", ctypes.c_int64),
                 ("n_cell_entries", ctypes.c_int64), ("grid_lo", ctypes.c_double * 3),
-                ("grid_hi", ctypes.c_double * 3), ("device_bytes", ctypes.c_size_t)]
+                ("grid_hi", ctypes.c_double * 3), ("device_bytes", ctypes.c_size_t),
+                ("setup_boxes_ms", ctypes.c_double), ("setup_grid_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -73,6 +75,8 @@ def lib() -> ctypes.CDLL:
             "fp_device_status": ([_vp, ctypes.POINTER(_int), _vp], _int),
             "fp_status_string": ([_int], ctypes.c_char_p),
             "fp_alu_peak": ([_int, _int, ctypes.POINTER(ctypes.c_double), _vp], _int),
+            "fp_set_timing": ([_vp, _int], _int),
+            "fp_kernel_times": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)], _int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -141,9 +145,41 @@ def fp_set_point_order(mesh, order: int) -> None:
     _check("fp_set_point_order", lib().fp_set_point_order(mesh, int(order)))
 
 
+def _find_shapes(mesh, pts, code, elem, r, dist2) -> int:
+    """Checks the shapes of a find call's tensors against the mesh's d and
+    dr (the C ABI sees only pointers and n, so a short output would be
+    written past its end): pts [n][d]; code, elem, dist2 at least n entries;
+    r [n][dr].  Returns n."""
+    info = fp_get_info(mesh)
+    if pts.dim() != 2 or pts.shape[1] != info.d:
+        raise ValueError(f"pts must have shape (n, {info.d}), got {tuple(pts.shape)}")
+    n = pts.shape[0]
+    for name, t in (("code", code), ("elem", elem), ("dist2", dist2)):
+        if t.numel() < n:
+            raise ValueError(f"{name} has {t.numel()} entries, need {n}")
+    if r.numel() < n * info.dr or (r.dim() == 2 and r.shape[1] != info.dr) or r.dim() > 2:
+        raise ValueError(f"r must have shape (n, {info.dr}) with n >= {n}, got {tuple(r.shape)}")
+    return n
+
+
+def _eval_shapes(mesh, code, elem, r, field, nc: int, out, field_N: int | None = None) -> int:
+    """As _find_shapes for an eval call: elem and r [n][dr] cover the n
+    entries of code, field holds nc * NE * field_N^dr values and out nc * n."""
+    info = fp_get_info(mesh)
+    n = code.shape[0] if code.dim() > 0 else 0
+    Nf = info.N if field_N is None else field_N
+    if elem.numel() < n or r.numel() < n * info.dr:
+        raise ValueError(f"elem and r must cover the {n} points of code")
+    if field.numel() < nc * info.NE * Nf ** info.dr:
+        raise ValueError(f"field has {field.numel()} values, need {nc} x {info.NE} x {Nf}^{info.dr}")
+    if out.numel() < nc * n:
+        raise ValueError(f"out has {out.numel()} values, need {nc} x {n}")
+    return n
+
+
 def fp_findpts(mesh, pts, code, elem, r, dist2, stream=None) -> None:
     import torch
-    n = pts.shape[0] if pts.dim() > 0 else 0
+    n = _find_shapes(mesh, pts, code, elem, r, dist2)
     _check("fp_findpts", lib().fp_findpts(
         mesh, _ptr(pts, torch.float64, "pts"), n, _ptr(code, torch.int32, "code"),
         _ptr(elem, torch.int32, "elem"), _ptr(r, torch.float64, "r"),
@@ -152,7 +188,7 @@ def fp_findpts(mesh, pts, code, elem, r, dist2, stream=None) -> None:
 
 def fp_findpts_stats(mesh, pts, code, elem, r, dist2, stats, stream=None) -> None:
     import torch
-    n = pts.shape[0] if pts.dim() > 0 else 0
+    n = _find_shapes(mesh, pts, code, elem, r, dist2)
     if stats.numel() < FP_NSTATS:
         raise ValueError(f"stats: need {FP_NSTATS} int64 values, got {stats.numel()}")
     _check("fp_findpts_stats", lib().fp_findpts_stats(
@@ -163,7 +199,7 @@ def fp_findpts_stats(mesh, pts, code, elem, r, dist2, stats, stream=None) -> Non
 
 def fp_eval(mesh, code, elem, r, field, nc: int, out, stream=None) -> None:
     import torch
-    n = code.shape[0]
+    n = _eval_shapes(mesh, code, elem, r, field, nc, out)
     _check("fp_eval", lib().fp_eval(
         mesh, _ptr(code, torch.int32, "code"), _ptr(elem, torch.int32, "elem"),
         _ptr(r, torch.float64, "r"), n, _ptr(field, torch.float64, "field"), int(nc),
@@ -172,7 +208,7 @@ def fp_eval(mesh, code, elem, r, field, nc: int, out, stream=None) -> None:
 
 def fp_eval_order(mesh, code, elem, r, field, field_order: int, nc: int, out, stream=None) -> None:
     import torch
-    n = code.shape[0]
+    n = _eval_shapes(mesh, code, elem, r, field, nc, out, field_N=int(field_order) + 1)
     _check("fp_eval_order", lib().fp_eval_order(
         mesh, _ptr(code, torch.int32, "code"), _ptr(elem, torch.int32, "elem"),
         _ptr(r, torch.float64, "r"), n, _ptr(field, torch.float64, "field"), int(field_order), int(nc),
@@ -190,7 +226,9 @@ def fp_findpts_host(mesh, pts, code, elem, r, dist2, field=None, nc: int = 0, ou
         if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous():
             raise ValueError(f"{name}: expected a contiguous CPU {dt} tensor")
         return ctypes.c_void_p(t.data_ptr())
-    n = pts.shape[0]
+    n = _find_shapes(mesh, pts, code, elem, r, dist2)
+    if field is not None and (out is None or out.numel() < int(nc) * n):
+        raise ValueError(f"out must hold {int(nc)} x {n} values")
     _check("fp_findpts_host", lib().fp_findpts_host(
         mesh, hp(pts, torch.float64, "pts"), n, hp(code, torch.int32, "code"), hp(elem, torch.int32, "elem"),
         hp(r, torch.float64, "r"), hp(dist2, torch.float64, "dist2"),
@@ -220,6 +258,19 @@ def fp_device_status(mesh, stream=None) -> int:
     s = _int(0)
     _check("fp_device_status", lib().fp_device_status(mesh, ctypes.byref(s), _stream(stream)))
     return s.value
+
+
+def fp_set_timing(mesh, on: bool) -> None:
+    _check("fp_set_timing", lib().fp_set_timing(mesh, int(bool(on))))
+
+
+def fp_kernel_times(mesh):
+    """(ms, calls): per stage FP_TIME_* the summed kernel milliseconds and
+    the number of intervals since the last read."""
+    ms = (ctypes.c_double * FP_NTIMES)()
+    calls = (_i64 * FP_NTIMES)()
+    _check("fp_kernel_times", lib().fp_kernel_times(mesh, ms, calls))
+    return list(ms), list(calls)
 
 
 def fp_alu_peak(which: int, iters: int = 4000, stream=None) -> float:
@@ -483,7 +534,7 @@ def fp_findpts_mixed_noalloc(mesh, pts, code, elem, r, dist2, stream=None) -> No
     f = lib().fp_findpts_mixed_noalloc
     f.argtypes = [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]
     f.restype = _int
-    n = pts.shape[0] if pts.dim() > 0 else 0
+    n = _find_shapes(mesh, pts, code, elem, r, dist2)
     _check("fp_findpts_mixed_noalloc", f(
         mesh, _ptr(pts, torch.float64, "pts"), n, _ptr(code, torch.int32, "code"),
         _ptr(elem, torch.int32, "elem"), _ptr(r, torch.float64, "r"),

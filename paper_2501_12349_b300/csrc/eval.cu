@@ -64,7 +64,8 @@ int eval_impl(fp_mesh m, const int32_t* code, const int32_t* elem, const double*
   if (n == 0 || nc == 0) return FP_OK;
   if (!code || !elem || !r || !field || !out) return FP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  return dispatch_shape(Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+  cudaEvent_t t0 = timer_mark(m, st);
+  const int rc = dispatch_shape(Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;
     (void)Dc;
     const int blocks = grid_for(n, kEvalThreads, 148 * 64);
@@ -72,6 +73,8 @@ int eval_impl(fp_mesh m, const int32_t* code, const int32_t* elem, const double*
                                                         m->status);
     return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
   });
+  timer_span(m, FP_TIME_EVAL, t0, timer_mark(m, st));
+  return rc;
 }
 
 }  // namespace

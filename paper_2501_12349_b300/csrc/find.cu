@@ -40,16 +40,24 @@ static int findpts_impl(fp_mesh m, const double* pts, int64_t n, int32_t* code, 
   if (ints > 0 && cudaMallocAsync((void**)&scratch, sizeof(int) * (size_t)ints, st) != cudaSuccess)
     return FP_ENOMEM;
   int* perm = nullptr;
+  cudaEvent_t t0 = fp::timer_mark(m, st), t1 = nullptr, t2 = nullptr;
   int rc = ordered ? fp::cell_order(m, pts, n, scratch + nq, &perm, st) : FP_OK;
   if (rc == FP_OK) {
     if (mixed) {
       rc = cudaMemsetAsync(scratch + n, 0, sizeof(int), st) == cudaSuccess ? FP_OK : FP_ELAUNCH;
+      t1 = fp::timer_mark(m, st);
       if (rc == FP_OK)
-        rc = fp::launch_mixed_with_queue(m, pts, perm, n, code, elem, r, dist2, scratch, scratch + n, s, st);
+        rc = fp::launch_mixed_with_queue(m, pts, perm, n, code, elem, r, dist2, scratch, scratch + n, s, st,
+                                         &t2);
     } else {
+      t1 = fp::timer_mark(m, st);
       rc = fp::find_f64(m, pts, perm, n, code, elem, r, dist2, s, st);
     }
   }
+  cudaEvent_t t3 = fp::timer_mark(m, st);
+  if (ordered) fp::timer_span(m, FP_TIME_ORDER, t0, t1);
+  fp::timer_span(m, FP_TIME_FIND, t1, mixed ? t2 : t3);
+  if (mixed) fp::timer_span(m, FP_TIME_FOLLOW, t2, t3);
   if (scratch) cudaFreeAsync(scratch, st);
   return rc;
 }

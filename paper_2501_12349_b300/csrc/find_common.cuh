@@ -687,9 +687,11 @@ struct BatchWork {
 
 int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
              int* elem, double* r, double* dist2, unsigned long long* stats, cudaStream_t st);
+// The two launches of the mixed path; with mid given and the mesh's timer
+// on, *mid is a timing event recorded between them.
 int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
                             int* elem, double* r, double* dist2, int* queue, int* qcount,
-                            unsigned long long* stats, cudaStream_t st);
+                            unsigned long long* stats, cudaStream_t st, cudaEvent_t* mid = nullptr);
 // One element shape of a batch (find_mixed.cu): the find kernel(s) over
 // all items; order (may be NULL) is the batch cell order of the points.
 int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,

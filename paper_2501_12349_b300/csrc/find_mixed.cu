@@ -397,12 +397,13 @@ namespace fp {
 // (capacity >= n entries) and zeroed counter; allocates nothing.
 int launch_mixed_with_queue(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
                             int* elem, double* r, double* dist2, int* queue, int* qcount,
-                            unsigned long long* stats, cudaStream_t st) {
+                            unsigned long long* stats, cudaStream_t st, cudaEvent_t* mid) {
   const DevMesh v = m->view();
   return dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
     constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
     k_find_mixed<N, D, DR><<<persistent_blocks(n, mixed_ctas(N, D, DR)), kFindThreads, 0, st>>>(
         v, m->basis, pts, pidx, n, code, elem, r, dist2, queue, qcount, stats);
+    if (mid) *mid = timer_mark(m, st);
     if (n <= kGroupMaxPoints)
       k_find_f64_group<N, D, DR><<<persistent_blocks(n, f64_ctas(N)), kFindThreads, 0, st>>>(
           v, m->basis, pts, queue, n, qcount, code, elem, r, dist2, fallback_stats(stats));

@@ -121,9 +121,15 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ counts, i
 }  // namespace fp
 
 // The library-owned mesh object behind the fp_mesh handle.
+namespace fp {
+struct KernelTimer;
+}
+
 struct fp_mesh_s {
   int d, dr, N, ne, M, NL;
   int64_t NE, ncell, nnz;
+  fp::KernelTimer* timer;  // per-kernel CUDA-event timing (fp_set_timing), or null
+  double setup_ms[2];      // k_boxes and the Psi_L build, CUDA events at setup
   fp_opts opts;
   int precision;
   double* coords;
@@ -145,6 +151,12 @@ namespace fp {
 // host helpers shared by the translation units
 int host_basis_tab(int N, BasisTab* tab);
 int check_mesh(const fp_mesh_s* m);
+// Kernel timing (timing.cu): with the mesh's timer on, timer_mark records an
+// event on st and returns it (null otherwise); timer_span files the interval
+// between two marks under a stage (FP_TIME_*); timer_free releases it all.
+cudaEvent_t timer_mark(const fp_mesh_s* m, cudaStream_t st);
+void timer_span(const fp_mesh_s* m, int stage, cudaEvent_t a, cudaEvent_t b);
+void timer_free(fp_mesh_s* m);
 }  // namespace fp
 
 #include <type_traits>

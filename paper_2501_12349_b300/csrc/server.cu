@@ -621,13 +621,55 @@ void worker_loop(fp_server_s* s) {
   }
 }
 
-void destroy_server(fp_server_s* s) {
+// Waits, with the tick deadline, for the work the server queued on its own
+// streams (not for anything else on the device): an event recorded on each
+// stream, polled with a sleep.  Returns false if the deadline passed.
+bool drain_server_streams(fp_server_s* s) {
+  std::vector<cudaStream_t> streams;
+  for (auto& t : s->slot) {
+    if (t.st) streams.push_back(t.st);
+    for (int f = 0; f < kTickForks; ++f)
+      if (t.fork[f]) streams.push_back(t.fork[f]);
+  }
+  if (s->up) streams.push_back(s->up);
+  if (s->down) streams.push_back(s->down);
+  std::vector<cudaEvent_t> evs;
+  for (cudaStream_t st : streams) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) continue;
+    if (cudaEventRecord(ev, st) != cudaSuccess) {
+      cudaEventDestroy(ev);
+      continue;
+    }
+    evs.push_back(ev);
+  }
+  const double limit = s->opts.tick_timeout_s > 0 ? s->opts.tick_timeout_s : 30.0;
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(limit));
+  bool done = false;
+  while (true) {
+    done = true;
+    for (cudaEvent_t ev : evs) done &= cudaEventQuery(ev) != cudaErrorNotReady;
+    if (done || Clock::now() > deadline) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);  // released once complete
+  return done;
+}
+
+// Stops the scheduler, waits (bounded) for the server's streams and frees
+// its resources.  If the wait runs out, the device and pinned buffers the
+// kernels may still use are left allocated (leaked) and FP_ETIMEDOUT is
+// returned, rather than blocking or freeing memory under a running kernel.
+int destroy_server(fp_server_s* s) {
   if (s->worker.joinable()) {
     s->stop = true;
     s->cv_work.notify_all();
     s->worker.join();
   }
-  cudaDeviceSynchronize();
+  if (!drain_server_streams(s)) {
+    s->stats.timeouts++;
+    return FP_ETIMEDOUT;
+  }
   for (auto& t : s->slot) {
     if (t.st) cudaStreamDestroy(t.st);
     if (t.done) cudaEventDestroy(t.done);
@@ -648,6 +690,7 @@ void destroy_server(fp_server_s* s) {
   if (s->up) cudaStreamDestroy(s->up);
   if (s->down) cudaStreamDestroy(s->down);
   cudaFree(s->arena.base);
+  return FP_OK;
 }
 
 }  // namespace
@@ -844,7 +887,7 @@ extern "C" int fp_server_get_stats(fp_server s, fp_server_stats* out) {
 
 extern "C" int fp_server_destroy(fp_server s) {
   if (!s) return FP_EINVAL;
-  fp::destroy_server(s);
+  const int rc = fp::destroy_server(s);
   delete s;
-  return FP_OK;
+  return rc;
 }

@@ -656,6 +656,7 @@ int dev_alloc(T** p, size_t count, size_t* bytes) {
 }
 
 void free_mesh_memory(fp_mesh_s* m) {
+  timer_free(m);
   cudaFree(m->coords);
   cudaFree(m->coords32);
   cudaFree(m->aabb);
@@ -711,12 +712,17 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
     return FP_ENOMEM;
   }
   int rc = FP_OK;
+  // setup timing (fp_mesh_info): k_boxes, and the Psi_L build
+  cudaEvent_t ev[4] = {};
+  bool timed = true;
+  for (auto& e : ev) timed &= cudaEventCreate(&e) == cudaSuccess;
   do {
     if (cudaMemcpyAsync(dtab, htab.data(), htab.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
         cudaSuccess) {
       rc = FP_ELAUNCH;
       break;
     }
+    if (timed) cudaEventRecord(ev[0], st);
     rc = dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
       constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
       k_boxes<N, D, DR><<<(unsigned)m->NE, kBoxThreads, 0, st>>>(
@@ -725,12 +731,14 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
       return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
     });
     if (rc != FP_OK) break;
+    if (timed) cudaEventRecord(ev[1], st);
     // grid bounds = union of the expanded AABBs
     double* dbounds = nullptr;
     if (cudaMalloc(&dbounds, 6 * sizeof(double)) != cudaSuccess) {
       rc = FP_ENOMEM;
       break;
     }
+    if (timed) cudaEventRecord(ev[2], st);
     k_grid_bounds<<<1, 1024, 0, st>>>(m->aabb, m->NE, m->d, dbounds);
     double hb[6];
     cudaError_t ce = cudaMemcpyAsync(hb, dbounds, sizeof(hb), cudaMemcpyDeviceToHost, st);
@@ -795,6 +803,7 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
     cudaMemsetAsync(counts, 0, ncell * sizeof(int), st);
     k_grid_scatter<1><<<eb, 256, 0, st>>>(m->aabb, m->NE, g, counts, m->cell_start, m->cell_elems);
     k_grid_sort<<<grid_for(ncell, 256, 148 * 16), 256, 0, st>>>(m->cell_start, ncell, m->cell_elems);
+    if (timed) cudaEventRecord(ev[3], st);
     if ((rc = dev_alloc(&m->box32, (size_t)m->NE * BOX32, &m->bytes)) != FP_OK) {
       cudaFree(counts);
       break;
@@ -806,6 +815,13 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
     if (ce != cudaSuccess) rc = FP_ELAUNCH;
   } while (0);
   cudaStreamSynchronize(st);
+  if (timed && rc == FP_OK) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess) m->setup_ms[0] = a;
+    if (cudaEventElapsedTime(&b, ev[2], ev[3]) == cudaSuccess) m->setup_ms[1] = b;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(dtab);
   cudaFree(dlin);
   return rc;
@@ -942,6 +958,8 @@ extern "C" int fp_get_info(fp_mesh m, fp_mesh_info* info) {
     info->grid_hi[c] = m->hi[c];
   }
   info->device_bytes = m->bytes;
+  info->setup_boxes_ms = m->setup_ms[0];
+  info->setup_grid_ms = m->setup_ms[1];
   return FP_OK;
 }
 

@@ -1,6 +1,6 @@
 """GPU (CUDA path, through the C ABI) against the FP64 oracle: boxes, Psi_L,
 find and eval on every element shape and order, small cases in full and
-the full-size 3D workload on a seeded sample."""
+the full-size 3D workload (10^6 points) in full."""
 import numpy as np
 import pytest
 
@@ -161,28 +161,38 @@ def test_every_order(fp, torch, shape, order):
     m.close()
 
 
-def test_config2_full_size_sampled(fp, torch):
-    """The full 32^3, p=4 workload (10^6 points) in one launch, as the
-    benchmark runs it; the oracle checks a seeded sample of 20,000 outputs,
-    and properties that hold at any size check the rest."""
+@pytest.fixture(scope="module")
+def config2_oracle():
+    """The full 32^3, p=4 workload (10^6 points) and the oracle's find and
+    eval of every point."""
     w = W.config2()
+    om = oracle.OracleMesh(w.coords, 3, 3, w.N)
+    o = om.findpts(w.pts)
+    u = om.eval(w.field, *o[:3])
+    return w, om, o, u
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_config2_full_size(fp, torch, config2_oracle, precision):
+    """The full 32^3, p=4 workload in one call, as the benchmark runs it
+    (cell order, persistent launch): every one of the 10^6 outputs against
+    the oracle, find and eval, in the FP64 path and in the mixed path."""
+    w, om, o, uo = config2_oracle
     m = gpu_mesh(fp, torch, w.coords, 3, 3, w.order)
+    if precision == "mixed":
+        m.set_precision(fp.FP_MIXED)
     pts_t = torch.from_numpy(w.pts).cuda()
     code, elem, r, dist2 = m.find(pts_t)
     u = m.eval(code, elem, r, torch.from_numpy(w.field).cuda())
     g = tuple(to_np(t) for t in (code, elem, r, dist2))
-    idx = np.sort(np.random.default_rng(12).choice(len(w.pts), 20000, replace=False))
-    om = oracle.OracleMesh(w.coords, 3, 3, w.N)
-    o = om.findpts(w.pts[idx])
-    compare_find(o, tuple(a[idx] for a in g), label="config2 sample")
-    compare_eval(w.field, om.NE, w.N ** 3, o[1], om.eval(w.field, *o[:3]), to_np(u)[:, idx], "config2 eval")
-    # every point: points inside the unit cube are INTERIOR (the mesh covers
-    # it exactly), dist2 of INTERIOR points ~ 0, NOT_FOUND only outside
+    res = compare_find(o, g, label=f"config2 {precision}")
+    assert res["n"] == 10 ** 6 and min(res["codes"]) > 0
+    # properties that do not rest on the oracle: the mesh covers the unit
+    # cube exactly, so points inside it are INTERIOR, and NOT_FOUND only
+    # happens outside
     inside = np.all((w.pts > 1e-9) & (w.pts < 1 - 1e-9), axis=1)
-    assert np.all(g[0][inside] == 0)
-    assert np.all(g[3][g[0] == 0] < 1e-20)
-    assert np.all(np.abs(g[2][g[0] != 2]) <= 1.0)
-    assert np.all(~inside[g[0] == 2])
+    assert np.all(g[0][inside] == 0) and np.all(~inside[g[0] == 2])
+    compare_eval(w.field, om.NE, w.N ** 3, o[1], uo, to_np(u), f"config2 {precision} eval")
     assert m.device_status() == 0
     m.close()
 
@@ -483,4 +493,30 @@ def test_points_at_interior_nodes(fp, torch, case, precision):
     assert np.array_equal(g[1], el)  # an interior node lies in no other element
     np.testing.assert_allclose(g[2], rn, atol=1e-10)
     assert m.device_status() == 0
+    m.close()
+
+
+def test_kernel_times(fp, torch):
+    """fp_set_timing / fp_kernel_times: per-stage CUDA-event intervals of the
+    timed calls only (cell order, find kernel, FP64 follow-up, eval), read
+    once and then started afresh."""
+    w = W.hex_config(14, 40000, 1, n=6)
+    m = gpu_mesh(fp, torch, w.coords, 3, 3, w.order)
+    pts = torch.from_numpy(w.pts).cuda()
+    fld = torch.from_numpy(w.field).cuda()
+    m.find(pts)  # not timed
+    fp.fp_set_timing(m.handle, True)
+    for prec in (fp.FP_F64, fp.FP_MIXED):
+        m.set_precision(prec)
+        c, e, r, d2 = m.find(pts)
+        m.eval(c, e, r, fld)
+    fp.fp_set_timing(m.handle, False)
+    m.find(pts)  # not timed
+    ms, calls = fp.fp_kernel_times(m.handle)
+    assert calls == [2, 2, 1, 2], calls
+    assert all(v > 0 for v in ms), ms
+    ms2, calls2 = fp.fp_kernel_times(m.handle)
+    assert calls2 == [0, 0, 0, 0] and ms2 == [0.0] * 4
+    info = m.info()
+    assert info.setup_boxes_ms > 0 and info.setup_grid_ms > 0
     m.close()

@@ -223,3 +223,62 @@ def test_tick_watchdog(fp, torch, resident):
     code, elem, r, d2, u = s2.wait(s2.submit(0, fp.FP_REQ_REMAP, rng.uniform(0, 1, (1000, 3))))
     assert np.all(code != 2)
     s2.close()
+
+
+@pytest.fixture(scope="module")
+def config5_scale():
+    """One resident mesh as config 5 serves them at its highest order:
+    27^3 = 19,683 hexes of order 7 (512 nodes each), a smooth deformation of
+    amplitude 0.25, a random degree-3 polynomial to remap and the nodal
+    velocity field of the particle requests, with the oracle's mesh."""
+    import oracle
+    coords = W.hex_mesh(27, 7, 0.25)
+    rng = np.random.default_rng(58)
+    fld, _ = W.polynomial_field(coords, rng, 3)
+    vel = W.velocity_field(coords)
+    return coords, fld, vel, oracle.OracleMesh(coords, 3, 3, 8)
+
+
+def oracle_particles(om, vel, x0, steps, dt):
+    """Explicit midpoint steps (the RK2 of Sec. 6.7's particle tracking)
+    driven by the oracle: find + eval of the nodal velocity at x, then at
+    the midpoint, advanced with numpy; returns the final positions and the
+    oracle's find there."""
+    x = x0.copy()
+    for _ in range(steps):
+        o = om.findpts(x)
+        xm = x + 0.5 * dt * om.eval(vel, *o[:3]).T
+        o = om.findpts(xm)
+        x = x + dt * om.eval(vel, *o[:3]).T
+    return x, om.findpts(x)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_server_matches_oracle_config5_scale(fp, torch, config5_scale, precision):
+    """Served requests on a config-5-sized mesh of order 7 against the
+    oracle: a remap request (20,000 points, 5% outside the domain) must
+    match the oracle's find + eval, and a 4-step particle request (5,000
+    particles, dt = 0.1 h / |u|max) must match the oracle-driven midpoint
+    rule: code and element exact, r within 1e-10, positions within 1e-10."""
+    coords, fld, vel, om = config5_scale
+    m = fp.Mesh(torch.from_numpy(coords).cuda(), 3, 3, 7)
+    s = fp.Server([(m, torch.from_numpy(fld).cuda(), torch.from_numpy(vel).cuda())],
+                  precision=fp.FP_MIXED if precision == "mixed" else fp.FP_F64)
+    rng = np.random.default_rng(59)
+    pts = rng.uniform(-0.017, 1.017, (20000, 3))
+    xp = rng.uniform(0.02, 0.98, (5000, 3))
+    dt = 0.1 * (1.0 / 27) / np.sqrt(1.01)
+    ra = s.submit(0, fp.FP_REQ_REMAP, pts)
+    rp = s.submit(0, fp.FP_REQ_PARTICLE, xp, rk_steps=4, dt=dt)
+    code, elem, r, d2, u = s.wait(ra, timeout_s=120)
+    o = om.findpts(pts)
+    res = compare_find(o, (code, elem, r, d2), label=f"served remap {precision}")
+    assert min(res["codes"]) > 0
+    compare_eval(fld, om.NE, 8 ** 3, o[1], om.eval(fld, *o[:3]), u, f"served remap eval {precision}")
+    pc, pe, pr, pd, x = s.wait(rp, timeout_s=120)
+    xo, oo = oracle_particles(om, vel, xp, 4, dt)
+    assert np.max(np.abs(x - xo)) < 1e-10
+    assert np.max(np.abs(x - xp)) > 0.3 * dt  # the particles moved
+    compare_find(oo, (pc, pe, pr, pd), label=f"served particles {precision}")
+    s.close()
+    m.close()

@@ -1,14 +1,17 @@
 """The allocation-free mixed find (fp_findpts_mixed_noalloc) against the
 allocating mixed find (fp_findpts with FP_MIXED), through the C ABI.
 
-Some callers cannot let a library allocate device memory (they reserve the
-GPU's memory up front, or cannot afford an allocation's synchronisation or
-failure mid-step); this entry point keeps its scratch in a fixed array
-inside the library.  The test checks two calls in a row on different point
-sets — the second must not see the first call's scratch contents — and
-that a size above the fixed limit is refused before anything runs.  This
-file is collected last and builds its own mesh, so it runs the same alone
-or after the other tests.
+Some callers cannot let a library allocate device memory: solvers that
+reserve the GPU's memory up front and run under a hard budget, and code
+that must not meet an allocation's implicit synchronisation or its possible
+failure in the middle of a time step.  This entry point keeps its scratch
+in a fixed array inside the library.  The test checks two calls in a row on
+different point sets (the second must not see the first call's scratch
+contents), that device memory in use does not change across a call, that a
+size above the fixed limit is refused before anything runs, and that
+outputs too short for the points are refused by the binding.  This file is
+collected last and builds its own mesh, so it runs the same alone or after
+the other tests.
 """
 import numpy as np
 import pytest
@@ -27,6 +30,20 @@ def _outputs(torch, n):
             torch.full((n,), -1.0, dtype=torch.float64, device=dev))
 
 
+def _device_memory_in_use(torch):
+    """(bytes the driver reports in use on the device, bytes in use in the
+    device's default stream-ordered pool, bytes torch's allocator holds)."""
+    from cuda.bindings import runtime as rt
+    free, total = torch.cuda.mem_get_info()
+    err, dev = rt.cudaGetDevice()
+    assert err == rt.cudaError_t.cudaSuccess
+    err, pool = rt.cudaDeviceGetDefaultMemPool(dev)
+    assert err == rt.cudaError_t.cudaSuccess
+    err, used = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
+    assert err == rt.cudaError_t.cudaSuccess
+    return total - free, int(used), torch.cuda.memory_allocated()
+
+
 def test_noalloc_matches_allocating_mixed_find():
     import torch
 
@@ -42,8 +59,13 @@ def test_noalloc_matches_allocating_mixed_find():
         pts = torch.from_numpy(np.ascontiguousarray(pts_np)).cuda()
         ref = tuple(to_np(t) for t in mesh.find(pts))  # the allocating entry point
         out = _outputs(torch, pts.shape[0])
+        torch.cuda.synchronize()
+        before = _device_memory_in_use(torch)
         fp.fp_findpts_mixed_noalloc(mesh.handle, pts, *out)
         torch.cuda.synchronize()
+        after = _device_memory_in_use(torch)
+        if call > 0:  # the first call on the device may load the library's module
+            assert after == before, (before, after)
         got = tuple(to_np(t) for t in out)
         compare_find(ref, got, label=f"no-alloc call {call}")
         assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
@@ -55,5 +77,16 @@ def test_noalloc_matches_allocating_mixed_find():
         fp.fp_findpts_mixed_noalloc(mesh.handle, big, *out)
     assert err.value.status == fp.FP_EINVAL
     assert int((out[0] != 7).sum().item()) == 0
+    # outputs shorter than the points, or points of the wrong dimension:
+    # refused by the binding before the library is called
+    pts = torch.from_numpy(np.ascontiguousarray(w.pts[:1000])).cuda()
+    code, elem, r, d2 = _outputs(torch, 1000)
+    with pytest.raises(ValueError):
+        fp.fp_findpts_mixed_noalloc(mesh.handle, pts, code, elem, r[:999], d2)
+    with pytest.raises(ValueError):
+        fp.fp_findpts_mixed_noalloc(mesh.handle, pts, code[:10], elem, r, d2)
+    with pytest.raises(ValueError):
+        fp.fp_findpts_mixed_noalloc(mesh.handle, pts[:, :2].contiguous(), code, elem, r, d2)
+    assert int((code != 7).sum().item()) == 0
     assert mesh.device_status() == 0
     mesh.close()
