@@ -9,12 +9,13 @@
 //     (values O(h), so the FP32 Jacobian keeps ~1e-7 relative accuracy).
 //  3. A candidate whose FP32 iteration converged strictly inside the element
 //     is parked for FP64 refinement: x(r) in FP64, the Gauss-Newton step
-//     solved in FP64 with the FP32 Jacobian (volumes) or the FP64 one
-//     (surfaces and lines, whose converged residual is not zero), repeated
-//     until the step is below the Newton tolerance (typically two FP64
-//     evaluations).  Parked lanes
-//     wait until most of their warp is parked, so the FP64 work runs with
-//     nearly full warps.
+//     solved with the FP32 Jacobian at the converged iterate (volumes) or
+//     the FP64 one (surfaces and lines, whose converged residual is not
+//     zero), repeated until the step is below the Newton tolerance.  For
+//     volumes the first correction stands when the step after it is
+//     estimated far below that tolerance (certified), so most points take
+//     one FP64 evaluation.  Parked lanes wait until most of their warp is
+//     parked, so the FP64 work runs with nearly full warps.
 //  4. A candidate the FP32 iteration leaves clearly outside (on the boundary
 //     with a distance far above FP32 rounding) is BORDER, as FP64 would find;
 //     the search continues with the next candidate.
@@ -30,8 +31,8 @@
 namespace fp {
 namespace {
 
-enum : int { X_IDLE = 0, X_SCAN = 1, X_NEWTON = 2, X_RESTORE = 3, X_PARK = 4, X_DONE = 5 };
-enum : int { X_INIT = 1, X_TRIAL = 2, X_REST = 3 };
+enum : int { X_IDLE = 0, X_SCAN = 1, X_NEWTON = 2, X_RESTORE = 3, X_PARK = 4, X_DONE = 5, X_CONV = 6 };
+enum : int { X_INIT = 1, X_TRIAL = 2, X_REST = 3, X_FINAL = 4 };
 
 constexpr float kTol32 = 1e-4f;    // FP32 phase: stop when |dr|_inf < kTol32 (the step taken
                                    // then leaves an error near the FP32 floor)
@@ -39,6 +40,9 @@ constexpr float kTau32 = 1e-5f;    // FP32 rounding-level acceptance factor
 constexpr float kBorder32 = 1e-4f; // "clearly outside": distance > kBorder32 * Xrel
 constexpr int kPark = 31;          // run the FP64 refinement with >= kPark lanes parked
 constexpr int kMaxRefine = 4;
+constexpr double kCertStep = 2e-11;  // volumes: accept the first FP64 correction when the
+                                     // next step is estimated below this (see certified)
+constexpr double kCertEdge = 1e-10;  // ... and the result is this far inside the element
 
 // The FP64 kernel that finishes the queued points counts into the second
 // half of the statistics array, so the two precisions' work stays separate.
@@ -77,6 +81,68 @@ __device__ __forceinline__ bool gauss_newton_step(const T* G, const T (&dx)[D], 
           H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
   }
   return spd_solve<DR, T>(H, b, s) && det > rel_det * dprod;
+}
+
+// Volumes: may the first FP64 correction s1 (step size mx) from the
+// converged FP32 iterate r0 stand as the result?  The FP64 iteration of
+// Sec. 3.2.1 stops once its proposed step is below the Newton tolerance;
+// with the residual at r0 taken in FP64 and the correction solved with the
+// FP32 Jacobian J~ evaluated at r0, the error after the correction is
+// e1 <= q / (1 - q) |s1| (inf-norms), q = |J~^-1| (|J~ - G(r0)| + L |e0| / 2),
+// and the next step would be about e1.  Two parts of q:
+//  * the curvature term |J~^-1| L |s1|, L the element's bound on the second
+//    derivatives of the map (setup: the nodes' distance from the map's
+//    tangent at r = 0 times the sums of |phi''|, |phi'| |phi'| of the basis;
+//    box32 slot 19), with |e0| <= 2 |s1| while q <= 1/2;
+//  * the relative error of the FP32 Jacobian and of the FP32 solve,
+//    estimated as 64 u cond(J~) with u = 2^-24 (an estimate, not a bound:
+//    the Jacobian's error measured on the deformed 32^3 mesh is a few
+//    u cond(J~)); the FP64 residual's rounding moves r by |J~^-1| times a
+//    few ulp of the coordinates, far below kCertStep.
+// Certified when that estimate of e1 is below kCertStep and every |r_j| is
+// below 1 - kCertEdge, so the code INTERIOR is the FP64 iteration's too.
+template <int D>
+__device__ __forceinline__ bool certified(const float* G, float curv, double mx, const double* rn) {
+  static_assert(D == 2 || D == 3, "volumes only");
+  float inv[D * D], det;
+  if constexpr (D == 2) {
+    det = G[0] * G[3] - G[1] * G[2];
+    inv[0] = G[3];
+    inv[1] = -G[1];
+    inv[2] = -G[2];
+    inv[3] = G[0];
+  } else {
+    inv[0] = G[4] * G[8] - G[5] * G[7];
+    inv[1] = G[2] * G[7] - G[1] * G[8];
+    inv[2] = G[1] * G[5] - G[2] * G[4];
+    inv[3] = G[5] * G[6] - G[3] * G[8];
+    inv[4] = G[0] * G[8] - G[2] * G[6];
+    inv[5] = G[2] * G[3] - G[0] * G[5];
+    inv[6] = G[3] * G[7] - G[4] * G[6];
+    inv[7] = G[1] * G[6] - G[0] * G[7];
+    inv[8] = G[0] * G[4] - G[1] * G[3];
+    det = G[0] * inv[0] + G[1] * inv[3] + G[2] * inv[6];
+  }
+  float nG = 0.f, nI = 0.f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      a += fabsf(G[i * D + j]);
+      b += fabsf(inv[i * D + j]);
+    }
+    nG = fmaxf(nG, a);
+    nI = fmaxf(nI, b);
+  }
+  nI = nI / fabsf(det) * 1.001f;  // covers the FP32 rounding of the adjugate
+  const float m = (float)mx;
+  const float q = 64.f * 5.9604645e-08f * nG * nI + nI * curv * m;
+  if (!(q < 0.5f) || !(q / (1.f - q) * m <= (float)kCertStep)) return false;
+  bool in = true;
+#pragma unroll
+  for (int j = 0; j < D; ++j) in &= fabs(rn[j]) < 1.0 - kCertEdge;
+  return in;
 }
 
 // The mixed-precision lane loop over a source of work (see find_f64.cuh).
@@ -182,9 +248,11 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
         need = true;
         break;
       }
-      // X_NEWTON: one FP32 step
+      // X_NEWTON: one FP32 step (X_CONV: the converged iterate, evaluated)
       bool done = false, converged = false;
-      if (l >= mp->max_iter) {
+      if (mode == X_CONV) {
+        done = converged = true;
+      } else if (l >= mp->max_iter) {
         done = true;
       } else {
         const bool beta = (l > 0) && at_bound<DR>(r);
@@ -201,7 +269,14 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
 #pragma unroll
           for (int j = 0; j < DR; ++j) r[j] = rn[j];
           ++cnt.v[1];
-          done = converged = true;
+          if constexpr (DR == D) {
+            // volumes: evaluate at the converged iterate, so that the FP64
+            // correction uses the FP32 Jacobian at that point (certified)
+            etype = X_FINAL;
+            need = true;
+          } else {
+            done = converged = true;
+          }
         } else {
           pred = predicted_decrease<D, DR, float>(G, dx, ds, used_beta, HS);
           if (!(pred > 0.f)) {
@@ -285,11 +360,16 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
         inside &= below_unit(rnn[j]);
         mx = fmax(mx, fabs(s[j]));
       }
+      bool cert = false;
+      if constexpr (DR == D) {
+        if (inside && nref == 0 && !(mx < mp->newton_tol))
+          cert = certified<D>(G, __ldg(mp->box32 + (int64_t)e * BOX32 + 19), mx, rnn);
+      }
       if (!inside) {
         queue[atomicAdd(qcount, 1)] = (int)w.global(item, pi);
         ++cnt.v[6];
         mode = X_IDLE;
-      } else if (mx < mp->newton_tol) {
+      } else if (mx < mp->newton_tol || cert) {
         double f = 0.0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -348,6 +428,9 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
           ++cnt.v[2];
           mode = X_RESTORE;
         }
+      } else if (etype == X_FINAL) {
+        F = Fn;
+        mode = X_CONV;
       } else {
         if (etype == X_INIT) {
           alpha = 1.f;

@@ -32,8 +32,9 @@
 namespace fp {
 
 // Record of one element in DevMesh::box32 (floats): lo[3] hi[3] c[3] A[9]
-// Xrel pad xc[3] T[9], where Xrel bounds |x - x_ref| over the element
-// (largest AABB half-width), xc = x(0) - x_ref and T is the OBB frame
+// Xrel curv xc[3] T[9], where Xrel bounds |x - x_ref| over the element
+// (largest AABB half-width), curv (volumes) bounds max_c sum_jk |d^2 x_c /
+// dr_j dr_k| over the element, xc = x(0) - x_ref and T is the OBB frame
 // (J_c^{-1} for volumes, [t1 t2 n]^{-1} for surfaces), so the first dr rows
 // of T (x - x(0)) are the reference coordinates of the linearised map.
 constexpr int BOX32 = 32;

@@ -116,6 +116,51 @@ int host_basis_tab(int N, BasisTab* tab) {
 
 namespace {
 
+// Sums of |phi_i^(k)(r)| over the N Lagrange bases, maximised over r in
+// [-1, 1] by dense sampling (20001 points, 2% added for the sampling), for
+// k = 0, 1, 2; from them the factor K such that, for an element whose nodal
+// values deviate by at most dev from an affine function of r, every second
+// derivative sum over (j, k) of |d^2 x_c / dr_j dr_k| is at most dev * K:
+// dr * L2 L0^(dr-1) (j = k) + dr (dr - 1) * L1^2 L0^(dr-2) (j != k).
+double curvature_factor(int N, int dr) {
+  double z[FP_MAX_N], wq[FP_MAX_N], w[FP_MAX_N];
+  gll_host(N, z, wq);
+  for (int i = 0; i < N; ++i) {
+    double p = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != i) p *= (z[i] - z[m]);
+    w[i] = 1.0 / p;
+  }
+  double L[3] = {0.0, 0.0, 0.0};
+  const int S = 20001;
+  for (int k = 0; k < S; ++k) {
+    const double x = -1.0 + 2.0 * k / (S - 1);
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < N; ++i) {
+      // value, first and second derivative of prod_{m != i} (x - z_m)
+      double p = 1.0, dp = 0.0, d2p = 0.0;
+      for (int m = 0; m < N; ++m) {
+        if (m == i) continue;
+        const double t = x - z[m];
+        d2p = d2p * t + 2.0 * dp;
+        dp = dp * t + p;
+        p = p * t;
+      }
+      a[0] += fabs(w[i] * p);
+      a[1] += fabs(w[i] * dp);
+      a[2] += fabs(w[i] * d2p);
+    }
+    for (int q = 0; q < 3; ++q) L[q] = std::max(L[q], a[q]);
+  }
+  for (double& v : L) v *= 1.02;
+  const double pure = L[2] * pow(L[0], dr - 1), mixed = dr > 1 ? L[1] * L[1] * pow(L[0], dr - 2) : 0.0;
+  return dr * pure + dr * (dr - 1) * mixed;
+}
+
+// Per-element doubles that k_boxes hands to k_box32: x(0) (3), the OBB frame
+// T (9), the curvature bound (1).
+constexpr int kLin = 16;
+
 // Device table layout (doubles) for the box kernel.
 struct TabLayout {
   int N, M;
@@ -282,8 +327,9 @@ __device__ void line_rotation(const double* t, double* R) {
 template <int N, int D, int DR>
 __global__ void __launch_bounds__(kBoxThreads)
     k_boxes(const double* __restrict__ coords, int64_t NE, const double* __restrict__ tab, int M,
-            BasisTab B, double tol, double* __restrict__ aabb, double* __restrict__ obb_c,
-            double* __restrict__ obb_A, double* __restrict__ linmap, int* status) {
+            BasisTab B, double tol, double curv_factor, double* __restrict__ aabb,
+            double* __restrict__ obb_c, double* __restrict__ obb_A, double* __restrict__ linmap,
+            int* status) {
   constexpr int NN = ipow(N, DR);
   // bounding pieces: the 6 faces of a hex, the 4 edges of a quad, the
   // element itself for a surface quad or a line
@@ -383,6 +429,27 @@ __global__ void __launch_bounds__(kBoxThreads)
     double s = 0.0;
     for (int q = 0; q < D; ++q) s += T[c * D + q] * (X[q * NN + n] - xc[q]);
     Xt[idx] = s;
+  }
+  if (DR == D) {
+    // volumes: the nodes' largest distance from the tangent map x(0) + J_c r
+    // at their reference coordinates (Ti holds J_c), for the curvature bound
+    // of the mixed path's certified refinement
+    double dv = 0.0;
+    for (int idx = tid; idx < D * NN; idx += blockDim.x) {
+      const int c = idx / NN, n = idx % NN;
+      const int id[3] = {n % N, (n / N) % N, n / (N * N)};
+      double a = X[idx] - xc[c];
+      for (int q = 0; q < DR; ++q) a -= Ti[c * D + q] * B.z[id[q]];
+      dv = fmax(dv, fabs(a));
+    }
+    dv = warp_max(dv);
+    if ((tid & 31) == 0) red[0][tid >> 5] = dv;
+  }
+  __syncthreads();
+  if (DR == D && tid == 0) {
+    double dv = red[0][0];
+    for (int w = 1; w < kBoxThreads / 32; ++w) dv = fmax(dv, red[0][w]);
+    linmap[e * kLin + 12] = dv * curv_factor * (1.0 + 1e-6);
   }
   __syncthreads();
   const double* c0 = tab + L.c0;
@@ -503,11 +570,12 @@ __global__ void __launch_bounds__(kBoxThreads)
       aabb[e * 2 * D + D + c] = mid[c] + hw[c];
     }
     for (int c = 0; c < D; ++c) {
-      linmap[e * 12 + c] = xc[c];
-      for (int q = 0; q < D; ++q) linmap[e * 12 + 3 + c * 3 + q] = T[c * D + q];
+      linmap[e * kLin + c] = xc[c];
+      for (int q = 0; q < D; ++q) linmap[e * kLin + 3 + c * 3 + q] = T[c * D + q];
     }
     if (DR == 1)  // the linear start of a line: r = t.(x - x_c) / |t|^2
-      for (int q = 0; q < D; ++q) linmap[e * 12 + 3 + q] = tlin[q];
+      for (int q = 0; q < D; ++q) linmap[e * kLin + 3 + q] = tlin[q];
+    if (DR != D) linmap[e * kLin + 12] = 0.0;
     expand(D, blo[1], bhi[1], tol, mid, hw);
     for (int c = 0; c < D; ++c) {
       double s = xc[c];
@@ -635,9 +703,10 @@ __global__ void k_box32(const double* __restrict__ aabb, const double* __restric
       for (int k = 0; k < d; ++k) o[9 + c * 3 + k] = (float)obb_A[(e * d + c) * d + k];
     }
     o[18] = (float)(X * (1.0 + 1e-6));
+    o[19] = (float)(lin[e * kLin + 12] * (1.0 + 1e-6));
     for (int c = 0; c < d; ++c) {
-      o[20 + c] = (float)(lin[e * 12 + c] - elem_ref(aabb, d, e, c));
-      for (int q = 0; q < d; ++q) o[23 + c * 3 + q] = (float)lin[e * 12 + 3 + c * 3 + q];
+      o[20 + c] = (float)(lin[e * kLin + c] - elem_ref(aabb, d, e, c));
+      for (int q = 0; q < d; ++q) o[23 + c * 3 + q] = (float)lin[e * kLin + 3 + c * 3 + q];
     }
   }
 }
@@ -707,7 +776,7 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
   double* dtab = nullptr;
   double* dlin = nullptr;  // per element x(0) and the OBB frame T, for box32
   FP_CUDA_TRY(cudaMalloc(&dtab, htab.size() * sizeof(double)));
-  if (cudaMalloc(&dlin, sizeof(double) * 12 * m->NE) != cudaSuccess) {
+  if (cudaMalloc(&dlin, sizeof(double) * kLin * m->NE) != cudaSuccess) {
     cudaFree(dtab);
     return FP_ENOMEM;
   }
@@ -726,8 +795,8 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
     rc = dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
       constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
       k_boxes<N, D, DR><<<(unsigned)m->NE, kBoxThreads, 0, st>>>(
-          m->coords, m->NE, dtab, m->M, m->basis, m->opts.bbox_tol, m->aabb, m->obb_c, m->obb_A,
-          dlin, m->status);
+          m->coords, m->NE, dtab, m->M, m->basis, m->opts.bbox_tol, curvature_factor(N, DR), m->aabb,
+          m->obb_c, m->obb_A, dlin, m->status);
       return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
     });
     if (rc != FP_OK) break;
