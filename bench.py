@@ -423,11 +423,36 @@ def projection_block(fp, W, torch, dev, st, flush, args):
     return res
 
 
+def surface_points(fp, torch, dev, mesh, w):
+    """Query points of a surface mesh (sphere or torus): x_e(r) of the
+    workload's (element, r) pairs, evaluated by the library's interpolation
+    of the coordinate field, and for the 1% of pairs with an offset, moved
+    0.1 h along the unit normal of the analytic surface at that point (it
+    differs from the element's normal by the interpolation error).  Input
+    preparation, outside any timed region."""
+    n = len(w.fwd_elem)
+    code = torch.zeros(n, dtype=torch.int32, device=dev)
+    elem = torch.from_numpy(w.fwd_elem).to(dev)
+    r = torch.from_numpy(np.ascontiguousarray(w.fwd_r)).to(dev)
+    x = mesh.eval(code, elem, r, torch.from_numpy(w.coords).to(dev)).T.contiguous()  # [n][3]
+    if "sphere" in w.name:
+        nrm = x / x.norm(dim=1, keepdim=True)
+    else:  # torus: from the tube's centre circle (radius 1 in the xy plane)
+        ring = x.clone()
+        ring[:, 2] = 0.0
+        ring = ring / ring.norm(dim=1, keepdim=True)
+        nrm = x - ring
+        nrm = nrm / nrm.norm(dim=1, keepdim=True)
+    off = torch.from_numpy(w.fwd_offset).to(dev)
+    return (x + off[:, None] * nrm).contiguous()
+
+
 def batch_block(fp, W, torch, dev, st, flush, args):
     """The 64-mesh workload (quads, hexes, sphere/torus surfaces, p = 2..7,
-    1e3-5e4 elements, 1e3-1e6 points each, scalar fields): one autotuned
-    graph launch per run, against the same work issued as separate per-mesh
-    fp_findpts + fp_eval calls; FP64 and mixed precision."""
+    1e3-5e4 elements, 1e3-1e6 points each, scalar fields; surface points 99%
+    x_e(r), 1% moved 0.1 h off the surface): one autotuned graph launch per
+    run, against the same work issued as separate per-mesh fp_findpts +
+    fp_eval calls; FP64 and mixed precision."""
     t0 = time.perf_counter()
     ws = W.config4()
     gen_s = time.perf_counter() - t0
@@ -435,7 +460,8 @@ def batch_block(fp, W, torch, dev, st, flush, args):
     meshes = [fp.Mesh(torch.from_numpy(w.coords).to(dev), w.d, w.dr, w.order) for w in ws]
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    entries = [(m, torch.from_numpy(w.pts).to(dev), torch.from_numpy(w.field).to(dev)) for m, w in zip(meshes, ws)]
+    entries = [(m, surface_points(fp, torch, dev, m, w) if w.dr < w.d else torch.from_numpy(w.pts).to(dev),
+                torch.from_numpy(w.field).to(dev)) for m, w in zip(meshes, ws)]
     total = sum(e[1].shape[0] for e in entries)
     res = {"workload": "64 meshes: quad2d/hex3d/sphere+torus surfaces, p=2..7, NE 1e3-5e4, 1e3-1e6 pts, nc=1",
            "meshes": len(ws), "points": total, "elements": int(sum(w.NE for w in ws)),

@@ -14,7 +14,9 @@
 // (points outside the grid, or with non-finite coordinates, go to an extra
 // last bucket) and counts the cells, a scan gives the bucket starts, and a
 // second pass scatters the point indices.  The order within a bucket is
-// whatever the atomics give; it affects only which lane handles a point.
+// whatever the atomics give; it affects only which lane handles a point, as
+// do the cells themselves, which are computed in FP32 (a point near a cell
+// face may land in the neighbouring bucket).
 #include "find_common.cuh"
 
 namespace fp {
@@ -22,6 +24,50 @@ namespace fp {
 namespace {
 
 constexpr int kCostClasses = 4;  // candidates 3+, 2, 1, 0
+
+// The order only decides which lane handles a point, so its buckets may be
+// computed approximately: in FP32, from each coordinate truncated to FP32
+// on the integer pipe (conversions from FP64 run at the FP64 pipe's rate
+// on this GPU, a small fraction of FP32's).  Non-finite values become NaN,
+// magnitudes beyond FP32 infinity, tiny ones zero.
+__device__ __forceinline__ float trunc_to_float(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e == 0x7ff) return __int_as_float(0x7fc00000);
+  const int fe = e - 1023 + 127;
+  if (fe >= 255) return __int_as_float((int)(sign | 0x7f800000u));
+  if (fe <= 0) return __int_as_float((int)sign);
+  return __int_as_float((int)(sign | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)));
+}
+
+// Psi_L cell of x (x32 its FP32 copy) in FP32 arithmetic, or -1 outside
+// the grid (or not finite): close to point_cell, which decides candidates.
+template <int D>
+struct CellF32 {
+  float lo[D], hi[D], scale[D];
+  int NL;
+  __device__ __forceinline__ explicit CellF32(const DevMesh& m) : NL(m.NL) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      lo[c] = (float)m.lo[c];
+      hi[c] = (float)m.hi[c];
+      scale[c] = (float)m.scale[c];
+    }
+  }
+  __device__ __forceinline__ int64_t operator()(const float (&x)[D]) const {
+    int64_t cell = 0, mul = 1;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      if (!(x[c] >= lo[c] && x[c] <= hi[c])) return -1;
+      const int k = (int)floorf((x[c] - lo[c]) * scale[c]);
+      cell += mul * (k < 0 ? 0 : (k >= NL ? NL - 1 : k));
+      mul *= NL;
+    }
+    return cell;
+  }
+};
 
 // Bucket of a point: its cost class, then its cell.  The class counts the
 // candidate elements whose boxes may hold the point (the FP32 box test,
@@ -33,15 +79,12 @@ template <int D>
 __global__ void __launch_bounds__(256)
     k_point_cells(const __grid_constant__ DevMesh m, int64_t ncell, const double* __restrict__ pts, int64_t n,
                   int* __restrict__ cellof, int* __restrict__ counts) {
+  const CellF32<D> cf(m);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double xs[D];
     float x32[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      xs[c] = __ldg(pts + i * D + c);
-      x32[c] = (float)xs[c];
-    }
-    const int64_t cell = point_cell<D>(m, xs);
+    for (int c = 0; c < D; ++c) x32[c] = trunc_to_float(__ldg(pts + i * D + c));
+    const int64_t cell = cf(x32);
     int k;
     if (cell < 0) {
       k = (int)(kCostClasses * (ncell + 1) - 1);
@@ -80,17 +123,13 @@ __global__ void __launch_bounds__(256)
     }
     const BatchItem& it = items[lo];
     const int64_t p = g - it.start;
-    double xs[D];
     float x32[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      xs[c] = __ldg(it.pts + p * D + c);
-      x32[c] = (float)xs[c];
-    }
+    for (int c = 0; c < D; ++c) x32[c] = trunc_to_float(__ldg(it.pts + p * D + c));
     int64_t ncell = 1;
 #pragma unroll
     for (int c = 0; c < D; ++c) ncell *= it.m.NL;
-    const int64_t cell = point_cell<D>(it.m, xs);
+    const int64_t cell = CellF32<D>(it.m)(x32);
     int cand = 0;
     if (cell >= 0) {  // the cost class, as in k_point_cells
       const int q0 = __ldg(it.m.cell_start + cell), q1 = __ldg(it.m.cell_start + cell + 1);
