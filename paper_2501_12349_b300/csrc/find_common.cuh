@@ -109,24 +109,35 @@ __device__ __forceinline__ bool in_boxes_f64(const DevMesh& m, int64_t e, const 
 // sum_k A_jk (x_k - c_k) by at most 6u sum_k |A_jk| (|x_k| + |c_k|); the FP64
 // computation of the same quantities is off by ~1e-16 of them.  Margins of
 // 4u and 16u are used, so a decision taken here equals the FP64 one.
+// The record (128-byte aligned) is read as 16-byte vectors: a scalar load
+// per value costs an L1 access per lane, and with the lanes of a warp on
+// different elements the L1 is the bound of the box loops; the AABB test
+// needs the first two vectors, the OBB test three more.
 template <int D>
 __device__ __forceinline__ int boxes_f32(const float* __restrict__ rec, const float (&x)[D]) {
+  const float4* r4 = reinterpret_cast<const float4*>(rec);
+  const float4 v0 = __ldg(r4), v1 = __ldg(r4 + 1);
+  float b[18];  // lo[3] hi[3] c[3] A[9]
+  b[0] = v0.x, b[1] = v0.y, b[2] = v0.z, b[3] = v0.w, b[4] = v1.x, b[5] = v1.y, b[6] = v1.z, b[7] = v1.w;
   int res = 1;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const float lo = __ldg(rec + c), hi = __ldg(rec + 3 + c);
+    const float lo = b[c], hi = b[3 + c];
     const float dl = x[c] - lo, dh = hi - x[c];
     const float ml = 2.3841858e-07f * (fabsf(x[c]) + fabsf(lo));  // 4u
     const float mh = 2.3841858e-07f * (fabsf(x[c]) + fabsf(hi));
     if (dl < -ml || dh < -mh) return 0;
     if (!(dl > ml && dh > mh)) res = 2;
   }
+  const float4 v2 = __ldg(r4 + 2), v3 = __ldg(r4 + 3), v4 = __ldg(r4 + 4);
+  b[8] = v2.x, b[9] = v2.y, b[10] = v2.z, b[11] = v2.w, b[12] = v3.x, b[13] = v3.y, b[14] = v3.z;
+  b[15] = v3.w, b[16] = v4.x, b[17] = v4.y;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     float v = 0.f, eb = 0.f;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const float a = __ldg(rec + 9 + j * 3 + k), cc = __ldg(rec + 6 + k);
+      const float a = b[9 + j * 3 + k], cc = b[6 + k];
       v = fmaf(a, x[k] - cc, v);
       eb = fmaf(fabsf(a), fabsf(x[k]) + fabsf(cc), eb);
     }

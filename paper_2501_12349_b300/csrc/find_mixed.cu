@@ -230,12 +230,15 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
         // start from the linearised map, r0 = clamp(T (x* - x(0))): the FP32
         // phase promises the converged result, not the FP64 path's iterates
         {
-          const float* rec = mp->box32 + (int64_t)e * BOX32;
+          // slots 20..31 of the record, xc[3] T[9], as three 16-byte vectors
+          const float4* r4 = reinterpret_cast<const float4*>(mp->box32 + (int64_t)e * BOX32 + 20);
+          const float4 a = __ldg(r4), b = __ldg(r4 + 1), c4 = __ldg(r4 + 2);
+          const float lin[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
           for (int j = 0; j < DR; ++j) {
             float v = 0.f;
 #pragma unroll
-            for (int c = 0; c < D; ++c) v = fmaf(__ldg(rec + 23 + j * 3 + c), xr[c] - __ldg(rec + 20 + c), v);
+            for (int c = 0; c < D; ++c) v = fmaf(lin[3 + j * 3 + c], xr[c] - lin[c], v);
             r[j] = fminf(1.f, fmaxf(-1.f, v));
           }
         }
