@@ -242,8 +242,8 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
     bi.ld = items[i].n;
     if (bi.field) c.has_field = true;
     if (bi.n > 0) {
-      bi.cell_base = c.buckets;
-      c.buckets += m->ncell + 1;
+      bi.key_base = c.buckets;
+      c.buckets += order_keys(m);
       c.items.push_back(bi);
       c.total += bi.n;
       if (m->opts.point_order != FP_ORDER_CELL) c.unordered = true;

@@ -659,7 +659,7 @@ struct BatchItem {
   int nc;
   double* out;        // [nc] components, component c at out + c * ld
   int64_t ld;
-  int64_t cell_base;  // first bucket of this item's Psi_L cells in the batch's cell order
+  int64_t key_base;   // first of this item's order keys (order_keys of its mesh) in the batch's order
 };
 
 // A batch of items of one element shape; the point sequence is the items'
@@ -709,12 +709,13 @@ int launch_batch_class(const BatchItem* items, int nitems, int64_t total, int N,
                        const BasisTab& B, int precision, int ctas_per_sm, int clog2, const int* order,
                        int* queue, int* qcount, unsigned long long* stats, cudaStream_t st);
 // Cell-grouped point order (order.cu): scratch of cell_order_ints ints;
-// *perm points into it.
+// *perm points into it.  order_keys: the keys a mesh takes per cost class.
+int64_t order_keys(const fp_mesh_s* m);
 int64_t cell_order_ints(const fp_mesh_s* m, int64_t n);
 int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, int** perm, cudaStream_t st);
 // The same for one element shape of a batch: the points of all items grouped
-// by cost class, then (item, Psi_L cell); buckets = sum over items of
-// (cells + 1), with each item's cell_base set; scratch of
+// by cost class, then (item, first candidate element); buckets = sum over
+// items of order_keys, with each item's key_base set; scratch of
 // batch_cell_order_ints(total, buckets) ints.
 int64_t batch_cell_order_ints(int64_t total, int64_t buckets);
 int batch_cell_order(const BatchItem* items, int nitems, int64_t total, int d, int64_t buckets, int* scratch,

@@ -1,22 +1,24 @@
-// Cell-grouped traversal of the query points.
+// Element-grouped traversal of the query points.
 //
 // The paper notes (Sec. 3.2, on the CPU implementation) that handling the
 // points of one element together improves memory locality.  On this GPU the
 // find kernels read each candidate element's coordinates (125 nodes x 3
-// components x 8 B at p = 4) once per Newton evaluation; with points in
-// random order the lanes of a warp touch 32 different elements and most of
-// those reads miss L1.  Grouping the points by their Psi_L cell makes the
-// lanes of a warp share candidate elements, so the reads become broadcasts
-// that hit L1.  The result of each point does not depend on the order, so
-// the outputs are bit-identical to those of the unordered traversal.
+// components at p = 4) once per Newton evaluation; with points in random
+// order the lanes of a warp touch 32 different elements and the L1 serves
+// one access per lane.  Grouping the points by the first candidate element
+// that the find kernels will search (found through the point's Psi_L cell
+// and the FP32 box test) makes the lanes of a warp share that element, so
+// its reads become broadcasts.  The result of each point does not depend on
+// the order, so the outputs are bit-identical to those of the unordered
+// traversal.
 //
-// The order is a counting sort by cell: one pass computes each point's cell
-// (points outside the grid, or with non-finite coordinates, go to an extra
-// last bucket) and counts the cells, a scan gives the bucket starts, and a
-// second pass scatters the point indices.  The order within a bucket is
-// whatever the atomics give; it affects only which lane handles a point, as
-// do the cells themselves, which are computed in FP32 (a point near a cell
-// face may land in the neighbouring bucket).
+// The order is a counting sort by key (cost class, element): one pass
+// computes each point's key (points outside the grid, or with non-finite
+// coordinates, take the last key) and counts the keys, a scan gives the
+// bucket starts, and a second pass scatters the point indices.  The order
+// within a bucket is whatever the atomics give; it affects only which lane
+// handles a point, as do the keys themselves, which are computed in FP32 (a
+// point on a box face may land in a neighbouring bucket).
 #include "find_common.cuh"
 
 namespace fp {
@@ -69,32 +71,42 @@ struct CellF32 {
   }
 };
 
-// Bucket of a point: its cost class, then its cell.  The class counts the
-// candidate elements whose boxes may hold the point (the FP32 box test,
-// undecided cases counted), 3 or more first: every candidate but the last
-// costs a Newton run, so points with many candidates are the slow ones, and
-// taking them first leaves cheap points for the end of the launch, where
-// lanes that run out of points wait for the slowest of their warp.
+// Bucket of a point: its cost class, then its first candidate element.
+// The class counts the candidate elements whose boxes may hold the point
+// (the FP32 box test, undecided cases counted), 3 or more first: every
+// candidate but the last costs a Newton run, so points with many candidates
+// are the slow ones, and taking them first leaves cheap points for the end
+// of the launch, where lanes that run out of points wait for the slowest of
+// their warp.  Within a class the points are grouped by the first candidate
+// (the element the find kernels search first, in Psi_L's ascending order),
+// so the lanes of a warp mostly evaluate the same element and its
+// coordinates are read once for all of them.  Key = class * (NE + 1) +
+// element (NE: no candidate); points outside the grid take the last key.
+template <int D>
+__device__ __forceinline__ int order_key(const DevMesh& m, const float (&x32)[D], int64_t nkeys) {
+  const int64_t cell = CellF32<D>(m)(x32);
+  if (cell < 0) return (int)(kCostClasses * nkeys - 1);
+  int cand = 0, first = (int)(nkeys - 1);
+  const int q0 = __ldg(m.cell_start + cell), q1 = __ldg(m.cell_start + cell + 1);
+  for (int q = q0; q < q1 && cand < kCostClasses - 1; ++q) {
+    const int el = __ldg(m.cell_elems + q);
+    if (boxes_f32<D>(m.box32 + (int64_t)el * BOX32, x32) != 0) {
+      if (cand == 0) first = el;
+      ++cand;
+    }
+  }
+  return (int)((kCostClasses - 1 - cand) * nkeys + first);
+}
+
 template <int D>
 __global__ void __launch_bounds__(256)
-    k_point_cells(const __grid_constant__ DevMesh m, int64_t ncell, const double* __restrict__ pts, int64_t n,
+    k_point_cells(const __grid_constant__ DevMesh m, int64_t nkeys, const double* __restrict__ pts, int64_t n,
                   int* __restrict__ cellof, int* __restrict__ counts) {
-  const CellF32<D> cf(m);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float x32[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) x32[c] = trunc_to_float(__ldg(pts + i * D + c));
-    const int64_t cell = cf(x32);
-    int k;
-    if (cell < 0) {
-      k = (int)(kCostClasses * (ncell + 1) - 1);
-    } else {
-      int cand = 0;
-      const int q0 = __ldg(m.cell_start + cell), q1 = __ldg(m.cell_start + cell + 1);
-      for (int q = q0; q < q1 && cand < kCostClasses - 1; ++q)
-        cand += boxes_f32<D>(m.box32 + (int64_t)__ldg(m.cell_elems + q) * BOX32, x32) != 0;
-      k = (int)((kCostClasses - 1 - cand) * (ncell + 1) + cell);
-    }
+    const int k = order_key<D>(m, x32, nkeys);
     cellof[i] = k;
     atomicAdd(counts + k, 1);
   }
@@ -126,17 +138,12 @@ __global__ void __launch_bounds__(256)
     float x32[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) x32[c] = trunc_to_float(__ldg(it.pts + p * D + c));
-    int64_t ncell = 1;
-#pragma unroll
-    for (int c = 0; c < D; ++c) ncell *= it.m.NL;
-    const int64_t cell = CellF32<D>(it.m)(x32);
-    int cand = 0;
-    if (cell >= 0) {  // the cost class, as in k_point_cells
-      const int q0 = __ldg(it.m.cell_start + cell), q1 = __ldg(it.m.cell_start + cell + 1);
-      for (int q = q0; q < q1 && cand < kCostClasses - 1; ++q)
-        cand += boxes_f32<D>(it.m.box32 + (int64_t)__ldg(it.m.cell_elems + q) * BOX32, x32) != 0;
-    }
-    const int k = (int)((kCostClasses - 1 - cand) * buckets + it.cell_base + (cell < 0 ? ncell : cell));
+    // the item's key in [0, kCostClasses * (NE + 1)), as in k_point_cells,
+    // spread over the batch: class * buckets + the item's base + element
+    const int64_t nk = it.m.NE + 1;
+    const int k1 = order_key<D>(it.m, x32, nk);
+    const int64_t cls = k1 / nk, el = k1 - cls * nk;
+    const int k = (int)(cls * buckets + it.key_base + el);
     key[g] = k;
     atomicAdd(counts + k, 1);
   }
@@ -207,7 +214,7 @@ int64_t batch_cell_order_ints(int64_t total, int64_t buckets) {
 
 int batch_cell_order(const BatchItem* items, int nitems, int64_t total, int d, int64_t buckets, int* scratch,
                      int** perm, cudaStream_t st) {
-  const int64_t nb = kCostClasses * buckets;  // cost class x (items' cells)
+  const int64_t nb = kCostClasses * buckets;  // cost class x (items' keys)
   int* p = scratch;          // [total]
   int* key = p + total;      // [total]
   int* counts = key + total; // [nb]
@@ -227,13 +234,15 @@ int batch_cell_order(const BatchItem* items, int nitems, int64_t total, int d, i
   return FP_OK;
 }
 
+int64_t order_keys(const fp_mesh_s* m) { return m->NE + 1; }
+
 int64_t cell_order_ints(const fp_mesh_s* m, int64_t n) {
-  const int64_t nb = kCostClasses * (m->ncell + 1);
+  const int64_t nb = kCostClasses * order_keys(m);
   return 2 * n + 2 * nb + 1 + 2 * scan_tiles(nb) + 1;
 }
 
 int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, int** perm, cudaStream_t st) {
-  const int64_t nb = kCostClasses * (m->ncell + 1);  // buckets: cost class x (cells and "outside")
+  const int64_t nb = kCostClasses * order_keys(m);  // buckets: cost class x (elements and "none")
   int* p = scratch;                  // [n]
   int* cellof = p + n;               // [n]
   int* counts = cellof + n;          // [nb], reused as the scatter cursors
@@ -243,9 +252,9 @@ int cell_order(const fp_mesh_s* m, const double* pts, int64_t n, int* scratch, i
   const DevMesh v = m->view();
   const int blocks = (int)((n + 255) / 256 < 8 * 148 ? (n + 255) / 256 : 8 * 148);
   if (m->d == 2)
-    k_point_cells<2><<<blocks, 256, 0, st>>>(v, m->ncell, pts, n, cellof, counts);
+    k_point_cells<2><<<blocks, 256, 0, st>>>(v, order_keys(m), pts, n, cellof, counts);
   else
-    k_point_cells<3><<<blocks, 256, 0, st>>>(v, m->ncell, pts, n, cellof, counts);
+    k_point_cells<3><<<blocks, 256, 0, st>>>(v, order_keys(m), pts, n, cellof, counts);
   FP_TRY(exclusive_scan(counts, nb, start, sc, st));
   FP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)nb, st));
   k_point_scatter<<<blocks, 256, 0, st>>>(cellof, n, start, counts, p);

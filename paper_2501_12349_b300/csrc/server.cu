@@ -405,12 +405,12 @@ int launch_tick(fp_server_s* s, TickSlot& t) {
       if (!m0) m0 = me.m;
       if (!base.count(q.mesh)) {
         base[q.mesh] = buckets;
-        buckets += me.m->ncell + 1;
+        buckets += order_keys(me.m);
       }
       BatchItem& bi = t.items_h[ni++];
       memset(&bi, 0, sizeof(bi));
       bi.m = me.m->view();
-      bi.cell_base = base[q.mesh];
+      bi.key_base = base[q.mesh];
       bi.pts = q.xs + tl.off * d;
       bi.n = tl.len;
       bi.start = total;
@@ -734,7 +734,7 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
   // bytes per point >= 72, so the budget bounds the points in flight
   const int64_t qcap = (int64_t)(o.mem_budget / 72) + 2 * 64 + 16;
   int64_t all_buckets = 0;
-  for (auto& me : s->meshes) all_buckets += me.m->ncell + 1;
+  for (auto& me : s->meshes) all_buckets += order_keys(me.m);
   // one order range per shape: the single-range size plus, per shape, its
   // own scan's constant part and the 64-int alignment
   const int64_t ocap = batch_cell_order_ints(std::min(qcap, o.tick_points), all_buckets) +
