@@ -530,8 +530,10 @@ def serve_block(fp, W, torch, dev, args):
     gen_s = time.perf_counter() - t0
     h_min = min(w.h for w in ws)
     dt = 0.1 * h_min / np.sqrt(1.01)
+    policy = fp.FP_SCHED_SLACK if args.serve_policy == "slack" else fp.FP_SCHED_SRPT
     srv = fp.Server(entries, mem_budget=8 << 30, max_active=64, precision=fp.FP_MIXED,
-                    tick_points=args.serve_tick_points)
+                    tick_points=args.serve_tick_points, policy=policy,
+                    slack_base=args.serve_slack_base, slack_factor=args.serve_slack_factor)
     rng = np.random.default_rng(5)
     nmax = 10 ** 6
     pool_r = torch.from_numpy(rng.uniform(-0.01, 1.01, (nmax, 3))).pin_memory()
@@ -568,7 +570,8 @@ def serve_block(fp, W, torch, dev, args):
 
     res = {"workload": "8 hex meshes p=3..7 NE 1e4-1e5; requests 1e2-1e6 pts, half remap, half particle (4 RK2 steps)",
            "generate_and_setup_s": gen_s, "precision": "mixed", "dt": dt,
-           "tick_points": args.serve_tick_points}
+           "tick_points": args.serve_tick_points, "policy": args.serve_policy,
+           "slack_base": args.serve_slack_base, "slack_factor": args.serve_slack_factor}
     burst = draw(args.serve_burst)
 
     def serial_f64(reqs):
@@ -687,6 +690,10 @@ def main():
     ap.add_argument("--serve-burst", type=int, default=200)
     ap.add_argument("--serve-tick-points", type=int, default=1 << 19,
                     help="points per server tick (fp_server_opts.tick_points)")
+    ap.add_argument("--serve-policy", default="slack", choices=["slack", "srpt"],
+                    help="server tick policy (fp_server_opts.policy)")
+    ap.add_argument("--serve-slack-base", type=float, default=float(1 << 19))
+    ap.add_argument("--serve-slack-factor", type=float, default=2.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

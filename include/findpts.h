@@ -301,10 +301,27 @@ typedef struct {
   double tick_timeout_s; /* host watchdog per tick: its requests fail with     */
                          /* FP_ETIMEDOUT (memory kept until the tick ends)     */
   int64_t tick_points;   /* points per tick (default 2^19): a request's stage  */
-                         /* is split into tiles, the requests with the least   */
-                         /* work left first; fewer points per tick lower the   */
+                         /* is split into tiles, filled in the order of the    */
+                         /* policy below; fewer points per tick lower the      */
                          /* latency of small requests and cost capacity        */
+  int policy;            /* FP_SCHED_SLACK (default) or FP_SCHED_SRPT          */
+  double slack_base;     /* FP_SCHED_SLACK: a request's target is slack_base + */
+  double slack_factor;   /* slack_factor x its size, in stage points (below)   */
 } fp_server_opts;
+
+/* Tick policies.  Work is counted in stage points (a point searched and
+ * interpolated once; a particle request of n points and k steps is
+ * (2k + 1) n of them), and time in the stage points the server has
+ * finished since a request was submitted (its age).
+ *   FP_SCHED_SRPT: the requests with the least work left in their current
+ *     stage first (small requests pass large ones; a large one can wait
+ *     long under heavy load).
+ *   FP_SCHED_SLACK: least slack first, slack = slack_base + slack_factor x
+ *     size - age - work left, so a request's priority grows as it waits,
+ *     in proportion to its size: small requests still go first, and a
+ *     large one is not held back without bound. */
+#define FP_SCHED_SRPT 0
+#define FP_SCHED_SLACK 1
 
 typedef struct {
   int64_t submitted, admitted, completed, cancelled, ticks, timeouts;
@@ -312,7 +329,9 @@ typedef struct {
   size_t bytes_in_use;
 } fp_server_stats;
 
-void fp_server_opts_default(fp_server_opts* opts); /* 1 GiB, 64 slots, FP_MIXED, 30 s, 2^19 */
+/* 1 GiB, 64 slots, FP_MIXED, 30 s, 2^19 points per tick, FP_SCHED_SLACK with
+ * slack_base 2^19 and slack_factor 2 */
+void fp_server_opts_default(fp_server_opts* opts);
 
 /* remap_fields[i] ([nc_remap[i]][NE][N^dr], device) and velocity[i]
  * ([d][NE][N^dr], device) may be NULL (arrays themselves may be NULL); they

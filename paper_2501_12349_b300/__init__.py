@@ -23,6 +23,7 @@ FP_ORDER_GIVEN, FP_ORDER_CELL = 0, 1
 FP_MAX_N = 8
 FP_NSTATS = 16
 FP_TIME_ORDER, FP_TIME_FIND, FP_TIME_FOLLOW, FP_TIME_EVAL, FP_NTIMES = 0, 1, 2, 3, 4
+FP_SCHED_SRPT, FP_SCHED_SLACK = 0, 1
 
 
 class FindptsError(RuntimeError):
@@ -392,7 +393,8 @@ FP_REQ_REMAP, FP_REQ_PARTICLE = 0, 1
 
 class FpServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("precision", ctypes.c_int),
-                ("tick_timeout_s", ctypes.c_double), ("tick_points", ctypes.c_int64)]
+                ("tick_timeout_s", ctypes.c_double), ("tick_points", ctypes.c_int64), ("policy", ctypes.c_int),
+                ("slack_base", ctypes.c_double), ("slack_factor", ctypes.c_double)]
 
 
 class FpServerStats(ctypes.Structure):
@@ -448,11 +450,18 @@ class Server:
     with fields as device tensors [nc][NE][N^dr]."""
 
     def __init__(self, entries, mem_budget: int = 1 << 30, max_active: int = 64, precision: int = FP_MIXED,
-                 tick_timeout_s: float = 30.0, tick_points: int = 1 << 19):
+                 tick_timeout_s: float = 30.0, tick_points: int = 1 << 19, policy: int | None = None,
+                 slack_base: float | None = None, slack_factor: float | None = None):
         L = _server_sig()
         o = fp_server_opts_default()
         o.mem_budget, o.max_active, o.precision, o.tick_timeout_s = mem_budget, max_active, precision, tick_timeout_s
         o.tick_points = tick_points
+        if policy is not None:
+            o.policy = policy
+        if slack_base is not None:
+            o.slack_base = slack_base
+        if slack_factor is not None:
+            o.slack_factor = slack_factor
         n = len(entries)
         self.meshes = [e[0] for e in entries]
         self._keep = entries

@@ -190,6 +190,7 @@ struct Request {
   int nc = 0;
   cudaEvent_t ev = nullptr;  // upload / download completion
   Clock::time_point t_submit, t_admit, t_done;
+  int64_t born = 0;  // stage points the server had finished at submission
 };
 
 struct MeshEntry {
@@ -246,6 +247,7 @@ struct fp_server_s {
   std::deque<int64_t> queued;
   std::unordered_map<int64_t, std::unique_ptr<fp::Request>> reqs;
   int64_t next_id = 1;
+  int64_t served = 0;  // stage points finished (tiles of completed ticks)
   int active = 0;
   std::atomic<bool> stop{false};
   std::thread worker;
@@ -362,12 +364,20 @@ int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& lau
 // held).  Returns 0 (nothing to do, or launched), or a negative status.
 int launch_tick(fp_server_s* s, TickSlot& t) {
   t.tiles.clear();
-  // tile-level interleaving: the requests with the least work left in their
-  // current stage go first, each takes what the tick's point budget leaves
-  std::vector<std::pair<int64_t, int64_t>> cand;  // (points left, id)
+  // tile-level interleaving: the requests in the policy's order, each takes
+  // what the tick's point budget leaves (FP_SCHED_SRPT: least work left in
+  // the current stage; FP_SCHED_SLACK: least slack, see findpts.h)
+  std::vector<std::pair<double, int64_t>> cand;  // (key, id)
   for (auto& kv : s->reqs) {
     const Request& q = *kv.second;
-    if (q.state == R_READY && q.status == FP_OK && q.next < q.n) cand.emplace_back(q.n - q.next, q.id);
+    if (!(q.state == R_READY && q.status == FP_OK && q.next < q.n)) continue;
+    double key = (double)(q.n - q.next);
+    if (s->opts.policy == FP_SCHED_SLACK) {
+      const double size = (double)q.n * q.nstages;
+      const double left = (double)q.n * (q.nstages - q.stage) - (double)q.next;
+      key = s->opts.slack_base + s->opts.slack_factor * size - (double)(s->served - q.born) - left;
+    }
+    cand.emplace_back(key, q.id);
   }
   if (cand.empty()) return 0;
   std::sort(cand.begin(), cand.end());
@@ -539,6 +549,7 @@ void complete_tick(fp_server_s* s, TickSlot& t, int status) {
     Request& q = *f->second;
     --q.inflight;
     q.done += tl.len;
+    s->served += tl.len;
     if (status != FP_OK && q.status == FP_OK) q.status = status;
     if (q.inflight > 0) continue;  // memory in use by the other tick
     if (q.status != FP_OK) {
@@ -703,6 +714,9 @@ extern "C" void fp_server_opts_default(fp_server_opts* o) {
   o->precision = FP_MIXED;
   o->tick_timeout_s = 30.0;
   o->tick_points = (int64_t)1 << 19;
+  o->policy = FP_SCHED_SLACK;
+  o->slack_base = (double)((int64_t)1 << 19);
+  o->slack_factor = 2.0;
 }
 
 extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* const* remap_fields,
@@ -716,7 +730,8 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
   fp_server_opts_default(&o);
   if (opts) o = *opts;
   if (o.mem_budget < ((size_t)1 << 20) || o.max_active < 1 || (o.precision != FP_F64 && o.precision != FP_MIXED) ||
-      o.tick_points < 1)
+      o.tick_points < 1 || (o.policy != FP_SCHED_SRPT && o.policy != FP_SCHED_SLACK) ||
+      !(o.slack_factor >= 0.0) || !(o.slack_base == o.slack_base))
     return FP_EINVAL;
   for (int i = 0; i < nm; ++i) {
     if (!meshes[i]) return FP_EINVAL;
@@ -802,6 +817,7 @@ extern "C" int fp_server_submit(fp_server s, int mesh, int kind, const double* p
   if (cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess) return FP_ELAUNCH;
   std::lock_guard<std::mutex> lk(s->mu);
   q->id = s->next_id++;
+  q->born = s->served;
   *req_id = q->id;
   s->queued.push_back(q->id);
   s->reqs[q->id] = std::move(q);
