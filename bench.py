@@ -692,8 +692,8 @@ def main():
                     help="points per server tick (fp_server_opts.tick_points)")
     ap.add_argument("--serve-policy", default="slack", choices=["slack", "srpt"],
                     help="server tick policy (fp_server_opts.policy)")
-    ap.add_argument("--serve-slack-base", type=float, default=float(1 << 19))
-    ap.add_argument("--serve-slack-factor", type=float, default=2.0)
+    ap.add_argument("--serve-slack-base", type=float, default=float(1 << 20))
+    ap.add_argument("--serve-slack-factor", type=float, default=4.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -330,7 +330,7 @@ typedef struct {
 } fp_server_stats;
 
 /* 1 GiB, 64 slots, FP_MIXED, 30 s, 2^19 points per tick, FP_SCHED_SLACK with
- * slack_base 2^19 and slack_factor 2 */
+ * slack_base 2^20 and slack_factor 4 */
 void fp_server_opts_default(fp_server_opts* opts);
 
 /* remap_fields[i] ([nc_remap[i]][NE][N^dr], device) and velocity[i]

@@ -715,8 +715,8 @@ extern "C" void fp_server_opts_default(fp_server_opts* o) {
   o->tick_timeout_s = 30.0;
   o->tick_points = (int64_t)1 << 19;
   o->policy = FP_SCHED_SLACK;
-  o->slack_base = (double)((int64_t)1 << 19);
-  o->slack_factor = 2.0;
+  o->slack_base = (double)((int64_t)1 << 20);
+  o->slack_factor = 4.0;
 }
 
 extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* const* remap_fields,

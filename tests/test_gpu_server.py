@@ -282,3 +282,28 @@ def test_server_matches_oracle_config5_scale(fp, torch, config5_scale, precision
     compare_find(oo, (pc, pe, pr, pd), label=f"served particles {precision}")
     s.close()
     m.close()
+
+
+def test_policies_same_results(fp, torch, resident):
+    """The tick policy (least slack, the default, or least work left in the
+    stage) changes only the order in which tiles are served: results are
+    identical; an unknown policy or a negative slack factor is refused."""
+    rng = np.random.default_rng(60)
+    pa = rng.uniform(-0.02, 1.02, (20000, 3))
+    pp = rng.uniform(0.05, 0.95, (6000, 3))
+    got = []
+    for pol in (fp.FP_SCHED_SLACK, fp.FP_SCHED_SRPT):
+        s = server_of(fp, resident, policy=pol, tick_points=4096)
+        ids = [s.submit(1, fp.FP_REQ_REMAP, pa), s.submit(2, fp.FP_REQ_PARTICLE, pp, rk_steps=2, dt=0.01)]
+        ids += [s.submit(k % 3, fp.FP_REQ_REMAP, rng.uniform(0, 1, (300, 3))) for k in range(6)]
+        got.append([[a.copy() for a in s.wait(i)] for i in ids[:2]])
+        for i in ids[2:]:
+            s.wait(i)
+        s.close()
+    for a, b in zip(got[0], got[1]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    for kw in ({"policy": 7}, {"slack_factor": -1.0}):
+        with pytest.raises(fp.FindptsError) as err:
+            server_of(fp, resident, **kw)
+        assert err.value.status == fp.FP_EINVAL
