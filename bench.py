@@ -49,7 +49,13 @@ KERNEL_SOURCES = {
     "k_find_mixed": ["find_mixed.cu", "find_f64.cuh", "find_common.cuh", "fp_basis.cuh", "beta_warp.cuh",
                      "fp_common.cuh", "find.cu", "order.cu"],
 }
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_find_f64 -s 3 -c 1 on
+    # bench.py --steps 2 --warmup 3 --skip-mixed --skip-batch --skip-serve --no-cpu-baseline
+    "k_find_f64": {"sha": "619c6b2e3c0184f9", "bytes": 720088576 + 72834048},
+    # the same with --precision mixed and -k regex:k_find_mixed
+    "k_find_mixed": {"sha": "27316fb2c87797f9", "bytes": 537069568 + 68320512},
+}
 
 
 def source_sha(kernel: str) -> str:
