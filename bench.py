@@ -493,6 +493,9 @@ def batch_block(fp, W, torch, dev, st, flush, args):
         b.autotune()
         tune_s = time.perf_counter() - t0
         ms_batch = timed(b.run)
+        b.set_fused(True)  # every shape in one persistent find launch
+        ms_fused = timed(b.run)
+        b.set_fused(False)
         outs = b.outputs
 
         def separate():
@@ -507,6 +510,7 @@ def batch_block(fp, W, torch, dev, st, flush, args):
             m.set_precision(fp.FP_F64)
         res[prec] = {"value": total / (ms_batch / 1e3), "unit": "points/s", "ms_per_run": ms_batch,
                      "separate_calls_ms": ms_sep, "speedup_vs_separate": ms_sep / ms_batch,
+                     "fused_launch_ms": ms_fused, "fused_vs_per_shape": ms_batch / ms_fused,
                      "autotune_s": tune_s,
                      "classes": [{"N": i.N, "d": i.d, "dr": i.dr, "items": i.n_items, "points": int(i.n_points),
                                   "ctas_per_sm": i.ctas_per_sm, "chunk": i.chunk_points,

@@ -251,6 +251,16 @@ int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_item* items, i
 /* Replays the captured graph on `stream` (asynchronous). */
 int fp_batch_run(fp_batch b, void* stream);
 
+/* The find of all shapes in ONE persistent launch (on = 1) instead of one
+ * persistent launch per shape (on = 0, the default): the shapes' point
+ * sequences are cut into tiles of 4096 points, which the CTAs pull from a
+ * counter, each tile searched by the lane loop of its shape (device-side
+ * dispatch over the compiled shapes); FP_MIXED adds each shape's FP64
+ * follow-up over its hand-over queue.  The point order, the evals and the
+ * results are the same in both forms.  Re-captures the graph; synchronous.
+ * Errors: FP_EINVAL, FP_ELAUNCH. */
+int fp_batch_set_fused(fp_batch b, int on);
+
 /* The launch shape autotuner: for every element shape of the plan, times the
  * shape's launches for CTAs per SM (the kernel's register-limited maximum
  * and one fewer: for FP_F64 {2, 3} up to order 5 and {1, 2} above; for

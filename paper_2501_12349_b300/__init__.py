@@ -303,8 +303,9 @@ def _batch_sig():
     L.fp_batch_free.argtypes = [_vp]
     L.fp_batch_num_classes.argtypes = [_vp]
     L.fp_batch_describe.argtypes = [_vp, _int, ctypes.POINTER(FpBatchClassInfo)]
+    L.fp_batch_set_fused.argtypes = [_vp, _int]
     for f in ("fp_batch_create", "fp_batch_run", "fp_batch_autotune", "fp_batch_free",
-              "fp_batch_num_classes", "fp_batch_describe"):
+              "fp_batch_num_classes", "fp_batch_describe", "fp_batch_set_fused"):
         getattr(L, f).restype = _int
     L._batch_sig = True
     return L
@@ -321,6 +322,10 @@ def fp_batch_create(meshes, items, precision: int = FP_F64, stream=None) -> _vp:
 
 def fp_batch_run(batch, stream=None) -> None:
     _check("fp_batch_run", _batch_sig().fp_batch_run(batch, _stream(stream)))
+
+
+def fp_batch_set_fused(batch, on: bool) -> None:
+    _check("fp_batch_set_fused", _batch_sig().fp_batch_set_fused(batch, int(bool(on))))
 
 
 def fp_batch_autotune(batch, stream=None) -> None:
@@ -371,6 +376,11 @@ class Batch:
 
     def autotune(self, stream=None):
         fp_batch_autotune(self.handle, stream)
+
+    def set_fused(self, on: bool):
+        """One persistent find launch over all element shapes (True) or one
+        per shape (False, the default)."""
+        fp_batch_set_fused(self.handle, on)
 
     def classes(self):
         return [fp_batch_describe(self.handle, i) for i in range(fp_batch_num_classes(self.handle))]

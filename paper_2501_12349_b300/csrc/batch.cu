@@ -109,6 +109,13 @@ struct ClassPlan {
 struct fp_batch_s {
   std::vector<fp::ClassPlan> classes;
   int precision = FP_F64;
+  // the fused form (one persistent find launch over all shapes)
+  bool fused = false;
+  fp::FusedClass* d_fclasses = nullptr;
+  fp::FusedTile* d_tiles = nullptr;
+  int ntiles = 0;
+  int* d_counter = nullptr;
+  int* status = nullptr;  // the first item's mesh status word
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t fork = nullptr;
@@ -141,10 +148,108 @@ void destroy_graph(fp_batch_s* b) {
   b->graph = nullptr;
 }
 
-// Captures every class's work, each on its own forked stream, into b->exec.
+// Points per tile of the fused launch: 32 per thread of a CTA.
+constexpr int kFusedTile = 32 * kFindThreads;
+
+// The fused form's class and tile tables: the classes' tiles, costliest
+// shape first (its points take longest), each class's tiles in its point
+// order (costly cost classes first).
+int build_fused_tables(fp_batch_s* b, cudaStream_t st) {
+  std::vector<FusedClass> fc;
+  std::vector<int> ids;
+  for (size_t i = 0; i < b->classes.size(); ++i) {
+    const ClassPlan& c = b->classes[i];
+    FusedClass f;
+    memset(&f, 0, sizeof(f));
+    f.items = c.d_items;
+    f.nitems = (int)c.items.size();
+    f.shape = shape_of(c.N, c.d, c.dr);
+    f.order = c.d_order;  // batch_cell_order puts the permutation at the scratch start
+    f.queue = c.d_queue;
+    f.qcount = c.d_queue ? c.d_queue + c.total : nullptr;
+    f.B = c.B;
+    fc.push_back(f);
+    if (c.total > 0) ids.push_back((int)i);
+  }
+  auto cost = [&](int i) {
+    const ClassPlan& c = b->classes[i];
+    return (double)ipow(c.N, c.dr) * (2 * c.N + 3) * c.d;
+  };
+  std::stable_sort(ids.begin(), ids.end(), [&](int a, int x) { return cost(a) > cost(x); });
+  std::vector<FusedTile> tiles;
+  for (int i : ids)
+    for (int64_t g = 0; g < b->classes[i].total; g += kFusedTile)
+      tiles.push_back({i, (int)std::min<int64_t>(kFusedTile, b->classes[i].total - g), g});
+  b->ntiles = (int)tiles.size();
+  if (fc.empty() || tiles.empty()) return FP_OK;
+  if (cudaMalloc(&b->d_fclasses, sizeof(FusedClass) * fc.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_tiles, sizeof(FusedTile) * tiles.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess)
+    return FP_ENOMEM;
+  FP_CUDA_TRY(cudaMemcpyAsync(b->d_fclasses, fc.data(), sizeof(FusedClass) * fc.size(), cudaMemcpyHostToDevice, st));
+  FP_CUDA_TRY(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(FusedTile) * tiles.size(), cudaMemcpyHostToDevice, st));
+  return FP_OK;
+}
+
+// The fused form: per class (forked) the point order and the queue counter,
+// then one persistent find launch over every class's tiles, then per class
+// (forked) the FP64 follow-up of FP_MIXED and the eval.
+int capture_fused(fp_batch_s* b) {
+  cudaStream_t st = b->cap;
+  FP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = FP_OK;
+  auto fork_classes = [&](auto&& body) {
+    if (rc == FP_OK && cudaEventRecord(b->fork, st) != cudaSuccess) rc = FP_ELAUNCH;
+    for (auto& c : b->classes) {
+      if (rc != FP_OK) break;
+      if (c.total == 0) continue;
+      if (cudaStreamWaitEvent(c.side, b->fork, 0) != cudaSuccess) {
+        rc = FP_ELAUNCH;
+        break;
+      }
+      rc = body(c);
+      if (rc == FP_OK && (cudaEventRecord(c.join, c.side) != cudaSuccess ||
+                          cudaStreamWaitEvent(st, c.join, 0) != cudaSuccess))
+        rc = FP_ELAUNCH;
+    }
+  };
+  fork_classes([&](ClassPlan& c) -> int {
+    if (b->precision == FP_MIXED) FP_CUDA_TRY(cudaMemsetAsync(c.d_queue + c.total, 0, sizeof(int), c.side));
+    int* order = nullptr;
+    if (c.d_order)
+      FP_TRY(batch_cell_order(c.d_items, (int)c.items.size(), c.total, c.d, c.buckets, c.d_order, &order, c.side));
+    return FP_OK;
+  });
+  if (rc == FP_OK && cudaMemsetAsync(b->d_counter, 0, sizeof(int), st) != cudaSuccess) rc = FP_ELAUNCH;
+  if (rc == FP_OK) rc = launch_fused(b->d_fclasses, b->d_tiles, b->ntiles, b->d_counter, b->precision, b->status, st);
+  fork_classes([&](ClassPlan& c) -> int {
+    if (b->precision == FP_MIXED)
+      FP_TRY(launch_batch_follow(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, c.d_queue,
+                                 c.d_queue + c.total, c.side));
+    if (c.has_field)
+      FP_TRY(launch_eval_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, c.side));
+    return FP_OK;
+  });
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != FP_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc != FP_OK ? rc : FP_ELAUNCH;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    destroy_graph(b);
+    return FP_ELAUNCH;
+  }
+  return FP_OK;
+}
+
+// Captures every class's work, each on its own forked stream, into b->exec
+// (the fused form: capture_fused).
 int capture(fp_batch_s* b) {
   cudaStream_t st = b->cap;
   destroy_graph(b);
+  if (b->fused) return capture_fused(b);
   FP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = FP_OK;
   if (cudaEventRecord(b->fork, st) != cudaSuccess) rc = FP_ELAUNCH;
@@ -185,6 +290,9 @@ void free_plan(fp_batch_s* b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_fclasses);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_counter);
 }
 
 }  // namespace
@@ -285,6 +393,10 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
       break;
     }
   }
+  if (rc == FP_OK) {
+    b->status = meshes[items[0].mesh]->status;
+    rc = build_fused_tables(b, st);
+  }
   if (rc == FP_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = FP_ELAUNCH;
   if (rc == FP_OK) rc = capture(b);
   if (rc != FP_OK) {
@@ -295,6 +407,12 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
   }
   *out = b;
   return FP_OK;
+}
+
+extern "C" int fp_batch_set_fused(fp_batch b, int on) {
+  if (!b) return FP_EINVAL;
+  b->fused = on != 0;
+  return fp::capture(b);
 }
 
 extern "C" int fp_batch_run(fp_batch b, void* stream) {

@@ -642,6 +642,9 @@ struct SingleWork {
     write_result<DR>(p, c, e, rr, d2, code, elem, r, dist2);
   }
   __device__ __forceinline__ int64_t global(int, int64_t p) const { return p; }
+  // the CTAs that share the point sequence in chunks, and this CTA's index
+  __device__ __forceinline__ int64_t ctas() const { return gridDim.x; }
+  __device__ __forceinline__ int64_t cta() const { return blockIdx.x; }
 };
 
 // One (mesh, points, outputs) item of a batch; `start` is the index of its
@@ -694,7 +697,50 @@ struct BatchWork {
     write_result<DR>(p, c, e, rr, d2, it.code, it.elem, it.r, it.dist2);
   }
   __device__ __forceinline__ int64_t global(int item, int64_t p) const { return items[item].start + p; }
+  __device__ __forceinline__ int64_t ctas() const { return gridDim.x; }
+  __device__ __forceinline__ int64_t cta() const { return blockIdx.x; }
 };
+
+// A tile of a batch class: points base .. base + n - 1 of the class's point
+// sequence, searched by one CTA alone (the fused launch, batch_fused.cu).
+template <int D, int DR>
+struct TileWork : BatchWork<D, DR> {
+  int64_t base;
+  __device__ __forceinline__ void locate(int64_t g, const DevMesh*& m, int& item, int64_t& p) const {
+    BatchWork<D, DR>::locate(base + g, m, item, p);
+  }
+  __device__ __forceinline__ int64_t ctas() const { return 1; }
+  __device__ __forceinline__ int64_t cta() const { return 0; }
+};
+
+// A class (element shape) of a batch as the fused launch sees it
+// (batch_fused.cu), and a tile of one class's point sequence.
+struct FusedClass {
+  const BatchItem* items;
+  int nitems;
+  int shape;          // shape_of(N, d, dr)
+  const int* order;   // the class's point order (global indices), or null
+  int* queue;         // FP_MIXED: the class's hand-over queue and its counter
+  int* qcount;
+  BasisTab B;
+};
+struct FusedTile {
+  int cls;
+  int n;
+  int64_t base;
+};
+// CTAs per SM of the fused launch: its register budget is that of the
+// costliest shape (hexes of order 6 and 7 need more than a third of the
+// register file per CTA of 128 threads).
+constexpr int kFusedCtas = 2;
+int shape_of(int N, int d, int dr);
+// One persistent launch over all tiles (counter zeroed by the caller).
+int launch_fused(const FusedClass* classes, const FusedTile* tiles, int ntiles, int* counter, int precision,
+                 int* status, cudaStream_t st);
+// FP_MIXED, one element shape of a batch: the FP64 kernel over the queued
+// global indices only (the launch_batch_class follow-up).
+int launch_batch_follow(const BatchItem* items, int nitems, int64_t total, int N, int d, int dr,
+                        const BasisTab& B, int* queue, int* qcount, cudaStream_t st);
 
 int find_f64(const fp_mesh_s* m, const double* pts, const int* pidx, int64_t n, int* code,
              int* elem, double* r, double* dist2, unsigned long long* stats, cudaStream_t st);

@@ -85,7 +85,7 @@ __device__ __forceinline__ void group_fetch(const Work& w, unsigned long long& s
   if (lane == 0) s0 = atomicAdd(&s_next, (unsigned long long)kGroupPoints);
   s0 = __shfl_sync(0xffffffffu, s0, 0);
   const unsigned long long s = s0 + (unsigned long long)(lane >> 2);
-  const int64_t chunk = (int64_t)(s0 >> clog2) * gridDim.x + blockIdx.x;
+  const int64_t chunk = (int64_t)(s0 >> clog2) * w.ctas() + w.cta();
   valid = false;
   if (chunk >= nchunks) {
     mode = M_DONE;
@@ -106,18 +106,29 @@ __device__ __forceinline__ void group_fetch(const Work& w, unsigned long long& s
   mode = M_SCAN;
 }
 
-// The FP64 lane loop over a source of work (SingleWork or BatchWork); all
-// meshes of one launch share N, D, DR and so the basis table B.
+// Shared memory of one CTA of the FP64 lane loop: the t-basis slabs, the
+// beta term's per-thread entries and per-warp scratch, the GLL
+// differentiation matrix and the CTA's point counter.
+template <int N, int D, int DR>
+struct F64Shared {
+  double slab[DR == 3 ? 2 * N * kFindThreads : 1];
+  double hs[beta_entries<DR>() * kFindThreads];
+  double bscr[(kFindThreads / 32) * kBetaScratch];
+  double dn[N * N];
+  unsigned long long next;
+};
+
+// The FP64 lane loop over a source of work (SingleWork, BatchWork or a tile
+// of one); all meshes of one call share N, D, DR and so the basis table B.
 template <int N, int D, int DR, class Work, bool kGroup = false>
-__device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, unsigned long long* stats) {
+__device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, unsigned long long* stats,
+                                              F64Shared<N, D, DR>& sh) {
   constexpr int NN = ipow(N, DR);
-  __shared__ double s_slab[DR == 3 ? 2 * N * kFindThreads : 1];
-  __shared__ double s_hs[beta_entries<DR>() * kFindThreads];
-  __shared__ double s_bscr[(kFindThreads / 32) * kBetaScratch];
-  __shared__ double s_dn[N * N];
-  const TSlots<N, double> ts{s_slab};
-  double* const wscr = s_bscr + (threadIdx.x >> 5) * kBetaScratch;
-  __shared__ unsigned long long s_next;
+  double* const s_hs = sh.hs;
+  double* const s_dn = sh.dn;
+  unsigned long long& s_next = sh.next;
+  const TSlots<N, double> ts{sh.slab};
+  double* const wscr = sh.bscr + (threadIdx.x >> 5) * kBetaScratch;
   if (threadIdx.x == 0) {
     s_next = 0;
 #pragma unroll
@@ -172,7 +183,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
         }
         if (mode == M_IDLE) {
           const unsigned long long s = atomicAdd(&s_next, 1ull);
-          const int64_t chunk = (int64_t)(s >> clog2) * gridDim.x + blockIdx.x;
+          const int64_t chunk = (int64_t)(s >> clog2) * w.ctas() + w.cta();
           if (chunk >= nchunks) {
             mode = M_DONE;
             break;
@@ -352,7 +363,8 @@ __global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
                int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
                double* __restrict__ dist2, int clog2, unsigned long long* stats) {
   const SingleWork<D, DR> w{&m, pts, pidx, n_dev ? (int64_t)*n_dev : n, code, elem, rout, dist2, clog2};
-  find_f64_loop<N, D, DR>(w, B, stats);
+  __shared__ F64Shared<N, D, DR> sh;
+  find_f64_loop<N, D, DR>(w, B, stats, sh);
 }
 
 // Every item of a batch (one element shape) in one persistent launch; gidx /
@@ -363,7 +375,8 @@ __global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
                      const int* __restrict__ gidx, const int* __restrict__ n_dev, const BasisTab B,
                      int clog2, unsigned long long* stats) {
   const BatchWork<D, DR> w{items, nitems, gidx, n_dev ? (int64_t)*n_dev : total, clog2};
-  find_f64_loop<N, D, DR>(w, B, stats);
+  __shared__ F64Shared<N, D, DR> sh;
+  find_f64_loop<N, D, DR>(w, B, stats, sh);
 }
 
 // Group mode (see find_f64_loop) over one mesh's points or a batch's, for
@@ -375,7 +388,8 @@ __global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
                      int* __restrict__ code, int* __restrict__ elem, double* __restrict__ rout,
                      double* __restrict__ dist2, unsigned long long* stats) {
   const SingleWork<D, DR> w{&m, pts, pidx, n_dev ? (int64_t)*n_dev : n, code, elem, rout, dist2, 5};
-  find_f64_loop<N, D, DR, SingleWork<D, DR>, true>(w, B, stats);
+  __shared__ F64Shared<N, D, DR> sh;
+  find_f64_loop<N, D, DR, SingleWork<D, DR>, true>(w, B, stats, sh);
 }
 
 template <int N, int D, int DR>
@@ -384,7 +398,8 @@ __global__ void __launch_bounds__(kFindThreads, f64_ctas(N))
                            const int* __restrict__ gidx, const int* __restrict__ n_dev, const BasisTab B,
                            unsigned long long* stats) {
   const BatchWork<D, DR> w{items, nitems, gidx, n_dev ? (int64_t)*n_dev : total, 5};
-  find_f64_loop<N, D, DR, BatchWork<D, DR>, true>(w, B, stats);
+  __shared__ F64Shared<N, D, DR> sh;
+  find_f64_loop<N, D, DR, BatchWork<D, DR>, true>(w, B, stats, sh);
 }
 
 }  // namespace fp

@@ -77,6 +77,17 @@ def test_batch_equals_single_and_oracle(fp, torch, config4_small, precision):
         compare_eval(w.field, om.NE, w.N ** w.dr, o[1], om.eval(w.field, *o[:3]), u, w.name + " eval")
         assert m.device_status() == 0
         m.set_precision(fp.FP_F64)
+    # the fused form (one persistent find launch over every shape) gives the
+    # same outputs bit for bit
+    first = [[t.clone() for t in o] for o in b.outputs]
+    b.set_fused(True)
+    for o in b.outputs:
+        o[0].fill_(7)
+    b.run()
+    torch.cuda.synchronize()
+    for f, o in zip(first, b.outputs):
+        for x, y in zip(f, o):
+            assert torch.equal(x, y)
     b.close()
 
 
@@ -137,36 +148,64 @@ def test_batch_cell_order_invariance(fp, torch, config4_small, precision):
             assert torch.equal(x, y)
 
 
+def workload_points_dev(fp, torch, mesh, w):
+    """As workload_points, with x_e(r) from the library's interpolation of
+    the coordinate field and the analytic surface normal (the benchmark's
+    recipe), on the device."""
+    if w.fwd_elem is None:
+        return torch.from_numpy(w.pts).cuda()
+    n = len(w.fwd_elem)
+    x = mesh.eval(torch.zeros(n, dtype=torch.int32, device="cuda"), torch.from_numpy(w.fwd_elem).cuda(),
+                  torch.from_numpy(np.ascontiguousarray(w.fwd_r)).cuda(), torch.from_numpy(w.coords).cuda()).T
+    if "sphere" in w.name:
+        nrm = x / x.norm(dim=1, keepdim=True)
+    else:
+        ring = x.clone()
+        ring[:, 2] = 0.0
+        ring = ring / ring.norm(dim=1, keepdim=True)
+        nrm = (x - ring) / (x - ring).norm(dim=1, keepdim=True)
+    return (x + torch.from_numpy(w.fwd_offset).cuda()[:, None] * nrm).contiguous()
+
+
 def test_batch_full_size_sampled(fp, torch):
     """The full 64-mesh workload (7.3 million points over 645k elements) in the
     launch configuration the benchmark times (one autotuned graph, FP64 and
-    mixed): on seven of the meshes, chosen across types, orders and sizes,
-    400 points spread over each point set match the oracle (code and element
+    mixed, surface points as the benchmark draws them): on every mesh, 2,000
+    points spread over its point set match the oracle (code and element
     exactly, r and dist2 to the FP64 tolerance, the interpolated field
-    relative to the field's scale)."""
+    relative to the field's scale); the fused form gives the same outputs
+    bit for bit on all points."""
     ws = W.config4()
-    pick = ["m16_hex3d_n15_p7", "m42_hex3d_n18_p5", "m33_hex3d_n17_p4", "m0_sphere_n35_p7",
-            "m61_torus_84x28_p3", "m6_quad2d_n33_p7", "m52_quad2d_n38_p4"]
-    by_name = {w.name: i for i, w in enumerate(ws)}
-    assert all(p in by_name for p in pick)
     meshes = [fp.Mesh(torch.from_numpy(w.coords).cuda(), w.d, w.dr, w.order) for w in ws]
-    entries = [(m, torch.from_numpy(w.pts).cuda(), torch.from_numpy(w.field).cuda()) for m, w in zip(meshes, ws)]
-    oms = {p: oracle.OracleMesh(ws[by_name[p]].coords, ws[by_name[p]].d, ws[by_name[p]].dr, ws[by_name[p]].N)
-           for p in pick}
+    entries = [(m, workload_points_dev(fp, torch, m, w), torch.from_numpy(w.field).cuda())
+               for m, w in zip(meshes, ws)]
+    sels = [np.linspace(0, e[1].shape[0] - 1, 2000).astype(np.int64) for e in entries]
+    ref = []
+    for (m, pt, fld), w, sel in zip(entries, ws, sels):
+        om = oracle.OracleMesh(w.coords, w.d, w.dr, w.N)
+        p = to_np(pt)[sel]
+        o = om.findpts(p)
+        ref.append((om, p, o, om.eval(w.field, *o[:3])))
     for prec in (fp.FP_F64, fp.FP_MIXED):
         b = fp.Batch(entries, prec)
         b.autotune()
         b.run()
         torch.cuda.synchronize()
-        for p in pick:
-            i = by_name[p]
-            w, om = ws[i], oms[p]
-            sel = np.linspace(0, len(w.pts) - 1, 400).astype(np.int64)
-            got = tuple(to_np(t)[sel] for t in b.outputs[i][:4])
-            o = om.findpts(w.pts[sel])
-            compare_find(o, got, label=f"full batch {prec} {p}", xscale=1.3, om=om, pts=w.pts[sel])
-            u = to_np(b.outputs[i][4])[..., sel]
-            compare_eval(w.field, om.NE, w.N ** w.dr, o[1], om.eval(w.field, *o[:3]), u, p + " eval")
+        for i, w in enumerate(ws):
+            om, p, o, uo = ref[i]
+            got = tuple(to_np(t)[sels[i]] for t in b.outputs[i][:4])
+            compare_find(o, got, label=f"full batch {prec} {w.name}", xscale=1.3, om=om, pts=p)
+            u = to_np(b.outputs[i][4])[..., sels[i]]
+            compare_eval(w.field, om.NE, w.N ** w.dr, o[1], uo, u, w.name + " eval")
+        first = [[t.clone() for t in o] for o in b.outputs]
+        b.set_fused(True)
+        for o in b.outputs:
+            o[0].fill_(7)
+        b.run()
+        torch.cuda.synchronize()
+        for f, o in zip(first, b.outputs):
+            for x, y in zip(f, o):
+                assert torch.equal(x, y)
         b.close()
     for m in meshes:
         assert m.device_status() == 0
