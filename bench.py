@@ -50,11 +50,11 @@ KERNEL_SOURCES = {
                      "fp_common.cuh", "find.cu", "order.cu"],
 }
 TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_find_f64 -s 3 -c 1 on
+    # ncu --set full -k regex:k_find_f64 -s 3 -c 1 on
     # bench.py --steps 2 --warmup 3 --skip-mixed --skip-batch --skip-serve --no-cpu-baseline
-    "k_find_f64": {"sha": "619c6b2e3c0184f9", "bytes": 720088576 + 72834048},
+    "k_find_f64": {"sha": "7baa73604ffe6efd", "bytes": 721328128 + 73786624},
     # the same with --precision mixed and -k regex:k_find_mixed
-    "k_find_mixed": {"sha": "27316fb2c87797f9", "bytes": 537069568 + 68320512},
+    "k_find_mixed": {"sha": "c19ac5211d96ac84", "bytes": 538218240 + 69063680},
 }
 
 
