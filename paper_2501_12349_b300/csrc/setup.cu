@@ -338,8 +338,10 @@ __global__ void __launch_bounds__(kBoxThreads)
   const TabLayout L(N, M);
   __shared__ double X[D * NN];
   __shared__ double Xt[D * NN];
-  __shared__ double u[N * N];
-  __shared__ double lin[3];
+  __shared__ double uu[2 * D * PIECE];
+  __shared__ unsigned char upos[2 * D * PIECE];
+  __shared__ double lin[2 * D][3];
+  __shared__ double rlo[kBoxThreads], rhi[kBoxThreads];
   __shared__ double T[9], Ti[9], xc[3], tlin[3];
   __shared__ double red[2][kBoxThreads / 32];
   __shared__ double blo[2][3], bhi[2][3];
@@ -455,113 +457,122 @@ __global__ void __launch_bounds__(kBoxThreads)
   const double* c0 = tab + L.c0;
   const double* c1 = tab + L.c1;
   const double* eta = tab + L.eta;
-  for (int kind = 0; kind < 2; ++kind) {
-    const double* src = kind ? Xt : X;
-    for (int c = 0; c < D; ++c) {
-      double tlo = INFINITY, thi = -INFINITY;
-      for (int piece = 0; piece < NPIECE; ++piece) {
-        // gather the piece's nodal values
-        for (int idx = tid; idx < PIECE; idx += blockDim.x) {
-          int n;
-          if (DR == 3) {
-            const int a = idx % N, b = idx / N, fixed = piece / 2;
-            const int val = (piece % 2) ? N - 1 : 0;
-            const int i = fixed == 0 ? val : a;
-            const int j = fixed == 0 ? a : (fixed == 1 ? val : b);
-            const int k = fixed == 2 ? val : b;
-            n = i + N * (j + N * k);
-          } else if (D == 3 || DR == 1) {
-            n = idx;
-          } else {
-            const int a = idx;
-            int i, j;
-            if (piece == 0) { i = a; j = 0; }
-            else if (piece == 1) { i = a; j = N - 1; }
-            else if (piece == 2) { i = 0; j = a; }
-            else { i = N - 1; j = a; }
-            n = i + N * j;
-          }
-          u[idx] = src[c * NN + n];
-        }
-        __syncthreads();
-        if (tid == 0) {
-          double a00 = 0.0, a10 = 0.0, a01 = 0.0;
-          if (PIECE == N) {
-            for (int a = 0; a < N; ++a) {
-              a00 += c0[a] * u[a];
-              a10 += c1[a] * u[a];
-            }
-          } else {
-            for (int b = 0; b < N; ++b)
-              for (int a = 0; a < N; ++a) {
-                const double v = u[a + N * b];
-                a00 += c0[a] * c0[b] * v;
-                a10 += c1[a] * c0[b] * v;
-                a01 += c0[a] * c1[b] * v;
-              }
-          }
-          lin[0] = a00;
-          lin[1] = a10;
-          lin[2] = a01;
-        }
-        __syncthreads();
-        for (int idx = tid; idx < PIECE; idx += blockDim.x) {
-          const int a = idx % N, b = idx / N;
-          u[idx] -= lin[0] + lin[1] * B.z[a] + (PIECE == N ? 0.0 : lin[2] * B.z[b]);
-        }
-        __syncthreads();
-        if (PIECE == N) {
-          const double* vlo = tab + L.vlo;
-          const double* vhi = tab + L.vhi;
-          for (int j = tid; j < M; j += blockDim.x) {
-            double l = lin[0] + lin[1] * eta[j], h = l;
-            for (int a = 0; a < N; ++a) {
-              const double p = u[a] * vlo[a * M + j], q = u[a] * vhi[a * M + j];
-              l += fmin(p, q);
-              h += fmax(p, q);
-            }
-            tlo = fmin(tlo, l);
-            thi = fmax(thi, h);
-          }
-        } else {
-          const double* pmin = tab + L.pmin;
-          const double* pmax = tab + L.pmax;
-          for (int g = tid; g < M * M; g += blockDim.x) {
-            const int k = g / M, l = g % M;
-            double lo = lin[0] + lin[1] * eta[k] + lin[2] * eta[l], hi = lo;
-            const double* pn = pmin + (size_t)g * N * N;
-            const double* px = pmax + (size_t)g * N * N;
-            for (int ab = 0; ab < N * N; ++ab) {
-              const double w = u[ab];
-              const double pl = __ldg(pn + ab), ph = __ldg(px + ab);
-              lo = fma(w, w >= 0.0 ? pl : ph, lo);
-              hi = fma(w, w >= 0.0 ? ph : pl, hi);
-            }
-            tlo = fmin(tlo, lo);
-            thi = fmax(thi, hi);
-          }
-        }
-        __syncthreads();
+  // Every (box kind, coordinate) combination of a piece at once: thread t
+  // works on combination t % NC at grid points t / NC, t / NC + PER, ...,
+  // so the 2 D bounds of a piece share its barriers (one piece gather,
+  // the compactions side by side) and nearly every thread is busy.
+  constexpr int NC = 2 * D;
+  constexpr int PER = kBoxThreads / NC;
+  const int kc = tid % NC, slot = tid / NC;
+  double tlo = INFINITY, thi = -INFINITY;
+  for (int piece = 0; piece < NPIECE; ++piece) {
+    // gather the piece's nodal values of every combination
+    for (int idx = tid; idx < NC * PIECE; idx += blockDim.x) {
+      const int q = idx / PIECE, a0 = idx % PIECE;
+      int n;
+      if (DR == 3) {
+        const int a = a0 % N, b = a0 / N, fixed = piece / 2;
+        const int val = (piece % 2) ? N - 1 : 0;
+        const int i = fixed == 0 ? val : a;
+        const int j = fixed == 0 ? a : (fixed == 1 ? val : b);
+        const int k = fixed == 2 ? val : b;
+        n = i + N * (j + N * k);
+      } else if (D == 3 || DR == 1) {
+        n = a0;
+      } else {
+        const int a = a0;
+        int i, j;
+        if (piece == 0) { i = a; j = 0; }
+        else if (piece == 1) { i = a; j = N - 1; }
+        else if (piece == 2) { i = 0; j = a; }
+        else { i = N - 1; j = a; }
+        n = i + N * j;
       }
-      tlo = warp_min(tlo);
-      thi = warp_max(thi);
-      if ((tid & 31) == 0) {
-        red[0][tid >> 5] = tlo;
-        red[1][tid >> 5] = thi;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double a = red[0][0], b = red[1][0];
-        for (int w = 1; w < kBoxThreads / 32; ++w) {
-          a = fmin(a, red[0][w]);
-          b = fmax(b, red[1][w]);
-        }
-        blo[kind][c] = a;
-        bhi[kind][c] = b;
-      }
-      __syncthreads();
+      uu[idx] = (q / D ? Xt : X)[(q % D) * NN + n];
     }
+    __syncthreads();
+    if (tid < NC) {  // the linear Legendre part, one combination per thread
+      const double* u = uu + tid * PIECE;
+      double a00 = 0.0, a10 = 0.0, a01 = 0.0;
+      if (PIECE == N) {
+        for (int a = 0; a < N; ++a) {
+          a00 += c0[a] * u[a];
+          a10 += c1[a] * u[a];
+        }
+      } else {
+        for (int b = 0; b < N; ++b)
+          for (int a = 0; a < N; ++a) {
+            const double v = u[a + N * b];
+            a00 += c0[a] * c0[b] * v;
+            a10 += c1[a] * c0[b] * v;
+            a01 += c0[a] * c1[b] * v;
+          }
+      }
+      lin[tid][0] = a00;
+      lin[tid][1] = a10;
+      lin[tid][2] = a01;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NC * PIECE; idx += blockDim.x) {
+      const int q = idx / PIECE, a0 = idx % PIECE;
+      const int a = a0 % N, b = a0 / N;
+      const double v = uu[idx] - (lin[q][0] + lin[q][1] * B.z[a] + (PIECE == N ? 0.0 : lin[q][2] * B.z[b]));
+      uu[idx] = v;
+      upos[idx] = v >= 0.0;  // the sign decides which product bound is the lower one
+    }
+    __syncthreads();
+    if (slot < PER) {
+      const double* u = uu + kc * PIECE;
+      const double* ln = lin[kc];
+      if (PIECE == N) {
+        const double* vlo = tab + L.vlo;
+        const double* vhi = tab + L.vhi;
+        for (int j = slot; j < M; j += PER) {
+          double l = ln[0] + ln[1] * eta[j], h = l;
+          for (int a = 0; a < N; ++a) {
+            const double p = u[a] * vlo[a * M + j], q = u[a] * vhi[a * M + j];
+            l += fmin(p, q);
+            h += fmax(p, q);
+          }
+          tlo = fmin(tlo, l);
+          thi = fmax(thi, h);
+        }
+      } else {
+        const double* pmin = tab + L.pmin;
+        const double* pmax = tab + L.pmax;
+        const unsigned char* pos = upos + kc * PIECE;
+        for (int g = slot; g < M * M; g += PER) {
+          const int k = g / M, l = g % M;
+          double lo = ln[0] + ln[1] * eta[k] + ln[2] * eta[l], hi = lo;
+          const double* pn = pmin + (size_t)g * N * N;
+          const double* px = pmax + (size_t)g * N * N;
+          for (int ab = 0; ab < N * N; ++ab) {
+            const double w = u[ab];
+            const double pl = __ldg(pn + ab), ph = __ldg(px + ab);
+            const bool nonneg = pos[ab];
+            lo = fma(w, nonneg ? pl : ph, lo);
+            hi = fma(w, nonneg ? ph : pl, hi);
+          }
+          tlo = fmin(tlo, lo);
+          thi = fmax(thi, hi);
+        }
+      }
+    }
+    __syncthreads();
   }
+  rlo[tid] = tlo;
+  rhi[tid] = thi;
+  __syncthreads();
+  if (tid < NC) {
+    double a = INFINITY, b = -INFINITY;
+    for (int s2 = 0; s2 < PER; ++s2) {
+      a = fmin(a, rlo[s2 * NC + tid]);
+      b = fmax(b, rhi[s2 * NC + tid]);
+    }
+    blo[tid / D][tid % D] = a;
+    bhi[tid / D][tid % D] = b;
+  }
+  __syncthreads();
   if (tid == 0) {
     double mid[3], hw[3];
     expand(D, blo[0], bhi[0], tol, mid, hw);
