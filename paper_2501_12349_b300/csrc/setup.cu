@@ -341,9 +341,11 @@ __global__ void __launch_bounds__(kBoxThreads)
   __shared__ double uu[2 * D * PIECE];
   __shared__ unsigned char upos[2 * D * PIECE];
   __shared__ double lin[2 * D][3];
+  __shared__ double rows[2 * D][N][2];
   __shared__ double rlo[kBoxThreads], rhi[kBoxThreads];
   __shared__ double T[9], Ti[9], xc[3], tlin[3];
   __shared__ double red[2][kBoxThreads / 32];
+  __shared__ double sums[kBoxThreads / 32][12];
   __shared__ double blo[2][3], bhi[2][3];
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
@@ -352,29 +354,51 @@ __global__ void __launch_bounds__(kBoxThreads)
     X[idx] = coords[((int64_t)c * NE + e) * NN + n];
   }
   __syncthreads();
-  if (tid == 0) {
-    // centre x(0) and Jacobian J_c = G(0) (sum over all nodes)
+  {
+    // centre x(0) and Jacobian J_c = G(0): sums over all nodes, split over
+    // the threads (one lane doing them alone costs a full warp instruction
+    // of the FP64 pipe per product), then reduced over the warps
     double ph[N], dph[N];
     lagrange<N, double>(B.z, B.w, 0.0, ph, dph);
+    double part[3 + 9];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) part[q] = 0.0;
+    for (int n = tid; n < NN; n += blockDim.x) {
+      const int i = n % N, j = (n / N) % N, k = n / (N * N);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const double v = X[c * NN + n];
+        if (DR == 3) {
+          part[c] += v * ph[i] * ph[j] * ph[k];
+          part[3 + c * 3 + 0] += v * dph[i] * ph[j] * ph[k];
+          part[3 + c * 3 + 1] += v * ph[i] * dph[j] * ph[k];
+          part[3 + c * 3 + 2] += v * ph[i] * ph[j] * dph[k];
+        } else if (DR == 2) {
+          part[c] += v * ph[i] * ph[j];
+          part[3 + c * 3 + 0] += v * dph[i] * ph[j];
+          part[3 + c * 3 + 1] += v * ph[i] * dph[j];
+        } else {
+          part[c] += v * ph[i];
+          part[3 + c * 3 + 0] += v * dph[i];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      double v = part[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) sums[tid >> 5][q] = v;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
     double J[9];
     for (int c = 0; c < D; ++c) {
       double xv = 0.0, g[3] = {0.0, 0.0, 0.0};
-      for (int n = 0; n < NN; ++n) {
-        const int i = n % N, j = (n / N) % N, k = n / (N * N);
-        const double v = X[c * NN + n];
-        if (DR == 3) {
-          xv += v * ph[i] * ph[j] * ph[k];
-          g[0] += v * dph[i] * ph[j] * ph[k];
-          g[1] += v * ph[i] * dph[j] * ph[k];
-          g[2] += v * ph[i] * ph[j] * dph[k];
-        } else if (DR == 2) {
-          xv += v * ph[i] * ph[j];
-          g[0] += v * dph[i] * ph[j];
-          g[1] += v * ph[i] * dph[j];
-        } else {
-          xv += v * ph[i];
-          g[0] += v * dph[i];
-        }
+      for (int w = 0; w < kBoxThreads / 32; ++w) {
+        xv += sums[w][c];
+        for (int j = 0; j < DR; ++j) g[j] += sums[w][3 + c * 3 + j];
       }
       xc[c] = xv;
       for (int j = 0; j < DR; ++j) J[c * DR + j] = g[j];
@@ -491,26 +515,45 @@ __global__ void __launch_bounds__(kBoxThreads)
       uu[idx] = (q / D ? Xt : X)[(q % D) * NN + n];
     }
     __syncthreads();
-    if (tid < NC) {  // the linear Legendre part, one combination per thread
-      const double* u = uu + tid * PIECE;
-      double a00 = 0.0, a10 = 0.0, a01 = 0.0;
-      if (PIECE == N) {
+    // the linear Legendre part of every combination
+    if (PIECE == N) {
+      if (tid < NC) {
+        const double* u = uu + tid * PIECE;
+        double a00 = 0.0, a10 = 0.0;
         for (int a = 0; a < N; ++a) {
           a00 += c0[a] * u[a];
           a10 += c1[a] * u[a];
         }
-      } else {
-        for (int b = 0; b < N; ++b)
-          for (int a = 0; a < N; ++a) {
-            const double v = u[a + N * b];
-            a00 += c0[a] * c0[b] * v;
-            a10 += c1[a] * c0[b] * v;
-            a01 += c0[a] * c1[b] * v;
-          }
+        lin[tid][0] = a00;
+        lin[tid][1] = a10;
+        lin[tid][2] = 0.0;
       }
-      lin[tid][0] = a00;
-      lin[tid][1] = a10;
-      lin[tid][2] = a01;
+    } else {
+      // one thread per (combination, row b) sums over a, then one per
+      // combination over b
+      if (tid < NC * N) {
+        const int q = tid / N, b = tid % N;
+        const double* u = uu + q * PIECE + N * b;
+        double s0 = 0.0, s1 = 0.0;
+        for (int a = 0; a < N; ++a) {
+          s0 += c0[a] * u[a];
+          s1 += c1[a] * u[a];
+        }
+        rows[q][b][0] = s0;
+        rows[q][b][1] = s1;
+      }
+      __syncthreads();
+      if (tid < NC) {
+        double a00 = 0.0, a10 = 0.0, a01 = 0.0;
+        for (int b = 0; b < N; ++b) {
+          a00 += c0[b] * rows[tid][b][0];
+          a10 += c0[b] * rows[tid][b][1];
+          a01 += c1[b] * rows[tid][b][0];
+        }
+        lin[tid][0] = a00;
+        lin[tid][1] = a10;
+        lin[tid][2] = a01;
+      }
     }
     __syncthreads();
     for (int idx = tid; idx < NC * PIECE; idx += blockDim.x) {
