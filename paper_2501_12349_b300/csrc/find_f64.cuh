@@ -21,6 +21,7 @@
 //    one while the divergent part costs almost no FP64 issue slots.
 #pragma once
 #include "beta_warp.cuh"
+#include "coop_eval.cuh"
 #include "find_common.cuh"
 
 namespace fp {
@@ -316,13 +317,25 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
     }
     if (finished) break;
     // ---- warp-uniform evaluation of x(r) and G(r) -------------------------
+    // (hexes: with at most kCoopLanes lanes needing it, the whole warp
+    // evaluates for each of them in turn, bit-identically; see coop_eval.cuh)
+    bool coop = false;
+    if constexpr (DR == 3) coop = __popc(__ballot_sync(0xffffffffu, need)) <= kCoopLanes;
+    double xv[D];
+    if (coop) {
+      if constexpr (DR == 3) {
+        double re[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) re[j] = (etype == E_TRIAL) ? rn[j] : r[j];
+        coop_eval_hex<N, D>(need, mp->coords + (int64_t)e * NN, mp->cstride, B, re, xv, G);
+      }
+    }
     if (need) {
       double re[DR];
 #pragma unroll
       for (int j = 0; j < DR; ++j) re[j] = (etype == E_TRIAL) ? rn[j] : r[j];
-      double xv[D];
       if (etype == E_TRIAL) ++cnt.v[7];
-      eval_xG<N, D, DR, true, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, re, ts, xv, G);
+      if (!coop) eval_xG<N, D, DR, true, double>(mp->coords + (int64_t)e * NN, mp->cstride, B, re, ts, xv, G);
       double Fn = 0.0;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
