@@ -50,17 +50,20 @@ __device__ __forceinline__ void coop_eval_hex(bool want, const double* __restric
       const double* xe = Xs + c * css;
       double a[NS], b[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        a[s] = 0.0;
-        b[s] = 0.0;
-        const int q = lane + 32 * s;
-        if (q < NP) {
-          const int j = q % N, k = q / N;
+      for (int s = 0; s < NS; ++s) a[s] = b[s] = 0.0;
+      // the shuffles are executed by every lane, outside the guarded loads
+      // (a warp collective must not sit in a branch that only some lanes take)
 #pragma unroll
-          for (int i = 0; i < N; ++i) {
+      for (int i = 0; i < N; ++i) {
+        const double pi = __shfl_sync(kAll, bph[i], 0), qi = __shfl_sync(kAll, bdph[i], 0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          const int q = lane + 32 * s;
+          if (q < NP) {
+            const int j = q % N, k = q / N;
             const double v = __ldg(xe + (k * N + j) * N + i);
-            a[s] = fma(v, __shfl_sync(kAll, bph[i], 0), a[s]);
-            b[s] = fma(v, __shfl_sync(kAll, bdph[i], 0), b[s]);
+            a[s] = fma(v, pi, a[s]);
+            b[s] = fma(v, qi, b[s]);
           }
         }
       }
