@@ -36,14 +36,14 @@ __device__ __forceinline__ void coop_eval_hex(bool want, const double* __restric
         __shfl_sync(kAll, reinterpret_cast<unsigned long long>(X), src));
     const int64_t css = __shfl_sync(kAll, (long long)cs, src);
     // lane d < 3 evaluates the basis along direction d at the owner's r_d
-    // (the same lagrange call as the owner's own evaluation); the others
+    // (the same basis call as the owner's own evaluation); the others
     // take the values by shuffles
     double rd = __shfl_sync(kAll, re[0], src);
     const double r1 = __shfl_sync(kAll, re[1], src), r2 = __shfl_sync(kAll, re[2], src);
     if (lane == 1) rd = r1;
     if (lane == 2) rd = r2;
     double bph[N], bdph[N];
-    lagrange<N, double>(B.z, B.w, rd, bph, bdph);
+    lagrange_sym<N, double>(B, rd, bph, bdph);
     const int kl = lane < N ? lane : 0;  // the row k whose j-sums this lane forms
 #pragma unroll 1
     for (int c = 0; c < D; ++c) {

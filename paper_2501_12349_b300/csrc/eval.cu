@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kEvalThreads)
     }
     double ph[DR][N], dph[DR][N] = {};  // dph unused: values only
 #pragma unroll
-    for (int j = 0; j < DR; ++j) lagrange_values<N, double>(B.z, B.w, __ldg(r + p * DR + j), ph[j]);
+    for (int j = 0; j < DR; ++j) lagrange_sym_values<N, double>(B, __ldg(r + p * DR + j), ph[j]);
     for (int c = 0; c < nc; ++c) {
       double v;
       map_eval<N, DR, 1, false, double>(field + c * cs + (int64_t)e * NN, 0, ph, dph, &v, nullptr);

@@ -471,9 +471,9 @@ __device__ __forceinline__ void eval_xG(const T* __restrict__ X, int64_t cs, con
 #pragma unroll
   for (int j = 0; j < DR; ++j) {
     if constexpr (WANT_G) {
-      lagrange<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), re[j], ph[j], dph[j]);
+      lagrange_sym<N, T>(B, re[j], ph[j], dph[j]);
     } else {
-      lagrange_values<N, T>(TabOf<T>::z(B), TabOf<T>::w(B), re[j], ph[j]);
+      lagrange_sym_values<N, T>(B, re[j], ph[j]);
 #pragma unroll
       for (int i = 0; i < N; ++i) dph[j][i] = T(0);
     }

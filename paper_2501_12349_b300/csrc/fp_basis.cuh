@@ -19,11 +19,15 @@ template <>
 struct TabOf<double> {
   static __device__ __forceinline__ const double* z(const BasisTab& b) { return b.z; }
   static __device__ __forceinline__ const double* w(const BasisTab& b) { return b.w; }
+  static __device__ __forceinline__ const double* z2(const BasisTab& b) { return b.z2; }
+  static __device__ __forceinline__ const double* w2(const BasisTab& b) { return b.w2; }
 };
 template <>
 struct TabOf<float> {
   static __device__ __forceinline__ const float* z(const BasisTab& b) { return b.zf; }
   static __device__ __forceinline__ const float* w(const BasisTab& b) { return b.wf; }
+  static __device__ __forceinline__ const float* z2(const BasisTab& b) { return b.z2f; }
+  static __device__ __forceinline__ const float* w2(const BasisTab& b) { return b.w2f; }
 };
 
 // phi_i(r) = w_i prod_{m != i} (r - z_m) and its derivative, from prefix and
@@ -65,6 +69,142 @@ __device__ __forceinline__ void lagrange_values(const T* z, const T* w, T r, T* 
     phi[i] = w[i] * (p[i] * s);
     s = s * d[i];
   }
+}
+
+// The same bases by the symmetry of the GLL nodes (z_{N-1-i} = -z_i): with
+// s = r^2 and f_m = s - z_m^2 for the K = N/2 pairs, (r - z_i)(r + z_i) = f_i,
+// so the node polynomial is [r] prod_m f_m ([r] only for odd N) and
+//   phi_i = Q_i (r + z_i),  phi_{N-1-i} = sigma Q_i (r - z_i),
+//   Q_i = w_i [r] L_i,  L_i = prod_{m != i} f_m  (i < K),
+// with sigma = (-1)^(N-1) the sign relating mirrored weights; for odd N the
+// middle basis is phi_K = w_K prod_m f_m.  Derivatives by the product rule
+// (df_m/dr = 2r, dL_i/ds = sum over m != i of the products without f_i, f_m).
+// Every factor is a difference of nearby exact quantities, as in the product
+// form, and at a node r = z_j (s = z_j^2 rounded as in the table, f_j = 0)
+// every basis but phi_j vanishes exactly.  At N = 5: 26 operations for
+// values and derivatives against 46 for the product form.
+template <int N, typename T>
+__device__ __forceinline__ void sym_leave_one_out(const T (&f)[N / 2], T (&L)[N / 2], T (&dL)[N / 2]) {
+  constexpr int K = N / 2;
+  if constexpr (K == 1) {
+    L[0] = T(1);
+    dL[0] = T(0);
+  } else if constexpr (K == 2) {
+    L[0] = f[1];
+    L[1] = f[0];
+    dL[0] = dL[1] = T(1);
+  } else {
+    T pre[K], dpre[K], suf[K], dsuf[K];
+    pre[1] = f[0];
+    dpre[1] = T(1);
+#pragma unroll
+    for (int i = 2; i < K; ++i) {
+      dpre[i] = fma(dpre[i - 1], f[i - 1], pre[i - 1]);
+      pre[i] = pre[i - 1] * f[i - 1];
+    }
+    suf[K - 2] = f[K - 1];
+    dsuf[K - 2] = T(1);
+#pragma unroll
+    for (int i = K - 3; i >= 0; --i) {
+      dsuf[i] = fma(dsuf[i + 1], f[i + 1], suf[i + 1]);
+      suf[i] = suf[i + 1] * f[i + 1];
+    }
+    L[0] = suf[0];
+    dL[0] = dsuf[0];
+    L[K - 1] = pre[K - 1];
+    dL[K - 1] = dpre[K - 1];
+#pragma unroll
+    for (int i = 1; i < K - 1; ++i) {
+      L[i] = pre[i] * suf[i];
+      dL[i] = fma(dpre[i], suf[i], pre[i] * dsuf[i]);
+    }
+  }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void lagrange_sym(const BasisTab& B, T r, T* phi, T* dphi) {
+  constexpr int K = N / 2;
+  constexpr bool kOdd = (N % 2) != 0;
+  const T* z = TabOf<T>::z(B);
+  const T* w = TabOf<T>::w(B);
+  const T* z2 = TabOf<T>::z2(B);
+  const T* w2 = TabOf<T>::w2(B);
+  const T s = r * r;
+  T f[K], L[K], dL[K];
+#pragma unroll
+  for (int m = 0; m < K; ++m) f[m] = s - z2[m];
+  sym_leave_one_out<N, T>(f, L, dL);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    T Q, dQ;
+    if constexpr (kOdd) {
+      const T wl = (K == 1) ? w[i] : w[i] * L[i];
+      Q = wl * r;
+      // dQ = w_i (L_i + 2 s dL_i)
+      if constexpr (K == 1) dQ = w[i];
+      else if constexpr (K == 2) dQ = fma(w2[i], s, wl);
+      else dQ = w[i] * fma(s + s, dL[i], L[i]);
+    } else {
+      Q = (K == 1) ? w[i] : w[i] * L[i];
+      // dQ = 2 w_i r dL_i
+      if constexpr (K == 1) dQ = T(0);
+      else if constexpr (K == 2) dQ = w2[i] * r;
+      else dQ = (w2[i] * r) * dL[i];
+    }
+    const T rp = r + z[i], rm = r - z[i];
+    phi[i] = Q * rp;
+    if constexpr (kOdd) {
+      phi[N - 1 - i] = Q * rm;
+    } else {
+      phi[N - 1 - i] = (-Q) * rm;
+    }
+    if constexpr (!kOdd && K == 1) {
+      dphi[i] = Q;
+      dphi[N - 1 - i] = -Q;
+    } else if constexpr (kOdd) {
+      dphi[i] = fma(dQ, rp, Q);
+      dphi[N - 1 - i] = fma(dQ, rm, Q);
+    } else {
+      dphi[i] = fma(dQ, rp, Q);
+      dphi[N - 1 - i] = fma(-dQ, rm, -Q);
+    }
+  }
+  if constexpr (kOdd) {
+    // phi_K = w_K prod_m f_m, dphi_K = 2 w_K r sum_m L_m
+    const T P = (K == 1) ? f[0] : L[0] * f[0];
+    phi[K] = w[K] * P;
+    T sL = L[0];
+#pragma unroll
+    for (int m = 1; m < K; ++m) sL += L[m];
+    dphi[K] = (K == 1) ? w2[K] * r : (w2[K] * r) * sL;
+  }
+}
+
+// Values only, in the symmetric form (at N = 5: 17 operations against 23).
+template <int N, typename T>
+__device__ __forceinline__ void lagrange_sym_values(const BasisTab& B, T r, T* phi) {
+  constexpr int K = N / 2;
+  constexpr bool kOdd = (N % 2) != 0;
+  const T* z = TabOf<T>::z(B);
+  const T* w = TabOf<T>::w(B);
+  const T* z2 = TabOf<T>::z2(B);
+  const T s = r * r;
+  T f[K], L[K], dL[K];
+#pragma unroll
+  for (int m = 0; m < K; ++m) f[m] = s - z2[m];
+  sym_leave_one_out<N, T>(f, L, dL);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    T Q = (K == 1) ? w[i] : w[i] * L[i];
+    if constexpr (kOdd) Q = Q * r;
+    phi[i] = Q * (r + z[i]);
+    if constexpr (kOdd) {
+      phi[N - 1 - i] = Q * (r - z[i]);
+    } else {
+      phi[N - 1 - i] = (-Q) * (r - z[i]);
+    }
+  }
+  if constexpr (kOdd) phi[K] = w[K] * ((K == 1) ? f[0] : L[0] * f[0]);
 }
 
 // Values, first and second derivatives.

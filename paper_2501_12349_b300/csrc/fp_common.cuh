@@ -47,11 +47,18 @@ __device__ __forceinline__ double elem_ref(const double* __restrict__ aabb, int 
 
 // GLL nodes z_i and barycentric weights w_i = 1 / prod_{m!=i} (z_i - z_m) of
 // one order, passed by value so the kernels read them from the constant bank.
+// The nodes are exactly symmetric about 0 (z_{N-1-i} = -z_i, the middle one
+// 0 for odd N) and so are the weights (w_{N-1-i} = (-1)^(N-1) w_i); z2 and
+// w2 hold z_m^2 (m < N/2) and 2 w_i for the symmetric form of the basis.
 struct BasisTab {
   double z[FP_MAX_N];
   double w[FP_MAX_N];
+  double z2[FP_MAX_N / 2];
+  double w2[FP_MAX_N];
   float zf[FP_MAX_N];
   float wf[FP_MAX_N];
+  float z2f[FP_MAX_N / 2];
+  float w2f[FP_MAX_N];
   double dn[FP_MAX_N * FP_MAX_N];  // dn[i * N + m] = phi_m'(z_i), the GLL differentiation matrix
 };
 

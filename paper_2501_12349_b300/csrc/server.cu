@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(128)
     }
     double ph[DR][N], dph[DR][N] = {};  // dph unused: values only
 #pragma unroll
-    for (int j = 0; j < DR; ++j) lagrange_values<N, double>(B.z, B.w, it.r[p * DR + j], ph[j]);
+    for (int j = 0; j < DR; ++j) lagrange_sym_values<N, double>(B, it.r[p * DR + j], ph[j]);
     for (int c = 0; c < it.nc; ++c) {
       double v;
       map_eval<N, DR, 1, false, double>(it.field + (c * NE + e) * NN, 0, ph, dph, &v, nullptr);

@@ -87,15 +87,31 @@ int host_basis_tab(int N, BasisTab* tab) {
   if (N < 2 || N > FP_MAX_N) return FP_EUNSUPPORTED;
   double z[FP_MAX_N], wq[FP_MAX_N];
   gll_host(N, z, wq);
+  // exact symmetry about 0, which the symmetric form of the basis relies on
+  for (int i = 0; i < N / 2; ++i) {
+    const double a = 0.5 * (z[N - 1 - i] - z[i]);
+    z[i] = -a;
+    z[N - 1 - i] = a;
+  }
+  if (N % 2) z[N / 2] = 0.0;
   memset(tab, 0, sizeof(*tab));
+  const double sigma = (N % 2) ? 1.0 : -1.0;  // (-1)^(N-1)
   for (int i = 0; i < N; ++i) {
     double p = 1.0;
     for (int m = 0; m < N; ++m)
       if (m != i) p *= (z[i] - z[m]);
     tab->z[i] = z[i];
-    tab->w[i] = 1.0 / p;
-    tab->zf[i] = (float)z[i];
-    tab->wf[i] = (float)(1.0 / p);
+    tab->w[i] = (i >= (N + 1) / 2) ? sigma * tab->w[N - 1 - i] : 1.0 / p;
+  }
+  for (int i = 0; i < N; ++i) {
+    tab->w2[i] = 2.0 * tab->w[i];
+    tab->zf[i] = (float)tab->z[i];
+    tab->wf[i] = (float)tab->w[i];
+    tab->w2f[i] = 2.0f * tab->wf[i];
+  }
+  for (int m = 0; m < N / 2; ++m) {
+    tab->z2[m] = tab->z[m] * tab->z[m];
+    tab->z2f[m] = tab->zf[m] * tab->zf[m];
   }
   // phi_m'(z_i) = (w_m / w_i) / (z_i - z_m) for m != i (differentiate the
   // product form of phi_m at a root of its other factors); the diagonal is
