@@ -423,7 +423,7 @@ __device__ __forceinline__ bool sign_bit(float v) { return __float_as_int(v) < 0
 // r_j = -1 with the gradient pointing out (g > 0), or r_j = +1 with g < 0.
 template <typename T>
 __device__ __forceinline__ bool held_at_bound(T r, T g) {
-  return is_unit(r) && (sign_bit(r) ? g > T(0) : g < T(0));
+  return is_unit(r) && (sign_bit(r) ? is_pos(g) : is_neg(g));
 }
 
 template <int DR, typename T>
@@ -523,9 +523,14 @@ __device__ __forceinline__ T newton_step(const T (&G)[D * DR], const T (&dx)[D],
       T s = T(0);
 #pragma unroll
       for (int c = 0; c < D; ++c) s += G[c * DR + j] * G[c * DR + k];
-      HGN[j][k] = HGN[k][j] = s;
-      H[j][k] = H[k][j] = beta ? s - HS[j][k] : s;
+      HGN[j][k] = HGN[k][j] = H[j][k] = H[k][j] = s;
     }
+  if (beta) {  // a branch of its own: skipped by warps where no lane holds beta
+#pragma unroll
+    for (int j = 0; j < DR; ++j)
+#pragma unroll
+      for (int k = j; k < DR; ++k) H[j][k] = H[k][j] = HGN[j][k] - HS[j][k];
+  }
   used_beta = beta;
   bool ok = masked_solve<DR, T>(H, held, g, step);
   if (!ok && beta) {
@@ -537,27 +542,38 @@ __device__ __forceinline__ T newton_step(const T (&G)[D * DR], const T (&dx)[D],
 #pragma unroll
     for (int j = 0; j < DR; ++j) step[j] = T(0);
   }
-  T mx = T(0);
+  // clip and projection with the bit-pattern tests (alpha > 0), and for
+  // double |dr|_inf as the largest magnitude's bit pattern (a NaN ignored,
+  // as fmax ignores it)
+  using FB = FBits<T>;
+  typename FB::I mx = 0;
+  T mxf = T(0);
   clipped = false;
 #pragma unroll
   for (int j = 0; j < DR; ++j) {
     T s = step[j];
-    if (s > alpha) {
+    if (above_nonneg(s, alpha)) {
       s = alpha;
       clipped = true;
     }
-    if (s < -alpha) {
+    if (above_nonneg(-s, alpha)) {
       s = -alpha;
       clipped = true;
     }
     T v = r[j] + s;
-    if (v > T(1)) v = T(1);
-    if (v < T(-1)) v = T(-1);
+    if (above_nonneg(v, T(1))) v = T(1);
+    if (above_nonneg(-v, T(1))) v = T(-1);
     rn[j] = v;
     ds[j] = v - r[j];
-    mx = fmax(mx, fabs(ds[j]));
+    if constexpr (std::is_same_v<T, float>) {
+      mxf = fmaxf(mxf, fabsf(ds[j]));
+    } else {
+      const auto a = FB::of(ds[j]) & FB::kAbs;
+      if (a <= FB::kInf && a > mx) mx = a;
+    }
   }
-  return mx;
+  if constexpr (std::is_same_v<T, float>) return mxf;
+  return FB::from(mx);
 }
 
 // -2 g.dr - dr^T H dr with H = G^T G (beta = 0: the same value as

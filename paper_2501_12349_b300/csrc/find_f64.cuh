@@ -246,7 +246,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
           double ds[DR];
           bool used_beta;
           const double mx = newton_step<D, DR>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
-          if (mx < mp->newton_tol) {
+          if (below_nonneg(mx, mp->newton_tol)) {
             // the last step is taken; dist2 from the linear model at r
             F = model_dist2<D, DR>(G, dx, ds);
 #pragma unroll
@@ -255,7 +255,7 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
             done = true;
           } else {
             pred = predicted_decrease<D, DR>(G, dx, ds, used_beta, HS);
-            if (!(pred > 0.0)) {
+            if (!is_pos(pred)) {
               done = true;
             } else {
               ++cnt.v[1];
@@ -268,8 +268,8 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
           bool inside = true;
 #pragma unroll
           for (int j = 0; j < DR; ++j) inside &= below_unit(r[j]);
-          if (DR < D) inside &= F < mp->dist_tol;
-          if (inside || F < bd) {
+          if (DR < D) inside &= below_nonneg(F, mp->dist_tol);
+          if (inside || below_nonneg(F, bd)) {
             bcode = inside ? FP_INTERIOR : FP_BORDER;
             be = e;
             bd = F;

@@ -360,6 +360,58 @@ __device__ __forceinline__ void map_eval_rolled(const T* __restrict__ X, int64_t
   }
 }
 
+// Order tests from the bit patterns, on the integer pipe (the FP64 one is
+// the find kernels' bound) and exact for every value: for IEEE values of one sign the integer order of the bit
+// patterns is the value order, and a NaN fails every test, as it fails the
+// floating-point comparison.
+template <typename T>
+struct FBits;
+template <>
+struct FBits<double> {
+  using I = long long;
+  static constexpr I kAbs = 0x7fffffffffffffffLL, kInf = 0x7ff0000000000000LL;
+  static __device__ __forceinline__ I of(double v) { return __double_as_longlong(v); }
+  static __device__ __forceinline__ double from(I i) { return __longlong_as_double(i); }
+};
+template <>
+struct FBits<float> {
+  using I = int;
+  static constexpr I kAbs = 0x7fffffff, kInf = 0x7f800000;
+  static __device__ __forceinline__ I of(float v) { return __float_as_int(v); }
+  static __device__ __forceinline__ float from(I i) { return __int_as_float(i); }
+};
+// (For float the plain comparisons are kept: the FP32 pipe is not the bound
+// of the FP32 phase, and the integer forms only add ALU instructions.)
+// v > 0
+template <typename T>
+__device__ __forceinline__ bool is_pos(T v) {
+  if constexpr (std::is_same_v<T, float>) return v > 0.0f;
+  const auto i = FBits<T>::of(v);
+  return i > 0 && i <= FBits<T>::kInf;
+}
+// v < 0
+template <typename T>
+__device__ __forceinline__ bool is_neg(T v) {
+  if constexpr (std::is_same_v<T, float>) return v < 0.0f;
+  const auto i = FBits<T>::of(v);
+  const auto a = i & FBits<T>::kAbs;
+  return i < 0 && a != 0 && a <= FBits<T>::kInf;
+}
+// v > c for c >= +0 (c not NaN)
+template <typename T>
+__device__ __forceinline__ bool above_nonneg(T v, T c) {
+  if constexpr (std::is_same_v<T, float>) return v > c;
+  const auto i = FBits<T>::of(v);
+  return i > FBits<T>::of(c) && i <= FBits<T>::kInf;
+}
+// a < b for a >= +0 and b >= +0, either of them possibly a NaN
+template <typename T>
+__device__ __forceinline__ bool below_nonneg(T a, T b) {
+  if constexpr (std::is_same_v<T, float>) return a < b;
+  const auto ia = FBits<T>::of(a), ib = FBits<T>::of(b);
+  return ia >= 0 && ia < ib && ib <= FBits<T>::kInf;
+}
+
 // Solves A s = b for a symmetric DR x DR matrix by cofactors when A is
 // positive definite (all leading principal minors > 0, the same sign test as
 // the pivots of a Cholesky factorisation); returns false otherwise.
@@ -371,7 +423,7 @@ __device__ __forceinline__ bool spd_solve(const T (&A)[DR][DR], const T (&b)[DR]
     return true;
   } else if constexpr (DR == 2) {
     const T det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-    if (!(A[0][0] > T(0)) || !(det > T(0))) return false;
+    if (!is_pos(A[0][0]) || !is_pos(det)) return false;
     const T inv = T(1) / det;
     s[0] = (A[1][1] * b[0] - A[0][1] * b[1]) * inv;
     s[1] = (A[0][0] * b[1] - A[1][0] * b[0]) * inv;
@@ -382,7 +434,7 @@ __device__ __forceinline__ bool spd_solve(const T (&A)[DR][DR], const T (&b)[DR]
     const T c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
     const T c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
     const T det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
-    if (!(A[0][0] > T(0)) || !(m2 > T(0)) || !(det > T(0))) return false;
+    if (!is_pos(A[0][0]) || !is_pos(m2) || !is_pos(det)) return false;
     const T c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
     const T c12 = A[0][2] * A[1][0] - A[0][0] * A[1][2];
     const T c22 = m2;
