@@ -371,6 +371,60 @@ __device__ __forceinline__ void node_start(const DevMesh& m, int e, int nb, cons
   }
 }
 
+// node_start for every lane of a converged warp that wants it, the warp
+// sharing the work: the D * DR entries of G of all starting lanes are tasks
+// spread over the 32 lanes (one N-term sum each, the same chain of FMAs in
+// the same order as node_start, so the result is bit-identical), written to
+// the owner's column of sg ([D * DR][kFindThreads]) and read back by it.
+// sl ([kFindThreads]) holds the warp's starting lanes by rank.  A lane
+// starting alone would otherwise charge the FP64 pipe all D * DR * N FMAs
+// of its node start as full-warp instructions.
+template <int N, int D, int DR>
+__device__ __forceinline__ void node_start_warp(bool want, const DevMesh& m, int e, int nb,
+                                                const double* __restrict__ dn, double* sg, int* sl,
+                                                double (&x)[D], double (&G)[D * DR]) {
+  constexpr unsigned kAll = 0xffffffffu;
+  constexpr int NN = ipow(N, DR);
+  constexpr int NT = D * DR;  // tasks per starting lane
+  const int lane = threadIdx.x & 31;
+  const int wbase = threadIdx.x & ~31;
+  const unsigned sm = __ballot_sync(kAll, want);
+  if (want) sl[wbase + __popc(sm & ((1u << lane) - 1u))] = lane;
+  __syncwarp();
+  const double* X = want ? m.coords + (int64_t)e * NN : m.coords;
+  const int64_t cs = m.cstride;
+  const int total = __popc(sm) * NT;
+  for (int t0 = 0; t0 < total; t0 += 32) {  // warp-uniform trip count
+    const int t = t0 + lane;
+    const bool act = t < total;
+    const int si = act ? t / NT : 0;
+    const int src = act ? sl[wbase + si] : lane;
+    const double* Xs = reinterpret_cast<const double*>(
+        __shfl_sync(kAll, reinterpret_cast<unsigned long long>(X), src));
+    const int64_t css = __shfl_sync(kAll, (long long)cs, src);
+    const int nbs = __shfl_sync(kAll, nb, src);
+    if (act) {
+      const int ent = t - si * NT;  // = c * DR + j, the entry of G
+      const int c = ent / DR, j = ent - c * DR;
+      const int idx = j == 0 ? nbs % N : (j == 1 ? (nbs / N) % N : nbs / (N * N));
+      const int st = j == 0 ? 1 : (j == 1 ? N : N * N);
+      const double* line = Xs + c * css + (nbs - idx * st);
+      const double* row = dn + idx * N;
+      double g = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) g = fma(__ldg(line + k * st), row[k], g);
+      sg[ent * kFindThreads + wbase + src] = g;
+    }
+  }
+  __syncwarp();
+  if (want) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = __ldg(X + c * cs + nb);
+#pragma unroll
+    for (int q = 0; q < NT; ++q) G[q] = sg[q * kFindThreads + threadIdx.x];
+  }
+}
+
 template <int D>
 __device__ __forceinline__ double aabb_scale(const DevMesh& m, int64_t e) {
   double X = 0.0;

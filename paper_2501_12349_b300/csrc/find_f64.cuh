@@ -12,9 +12,9 @@
 //    sum-factorised contraction that is most of the FP64 work), inlined once;
 //  * a candidate starts at its closest GLL node, where x is the node itself
 //    and G takes N terms per direction: the lanes that start one do it right
-//    after the warp's node search and take their first Newton step in a
-//    second bookkeeping pass, so their first full evaluation is already a
-//    trial step;
+//    after the warp's node search (the warp sharing the N-term sums of all
+//    of them) and take their first Newton step in a second bookkeeping
+//    pass, so their first full evaluation is already a trial step;
 //  * the box tests and the closest-node search, done by whichever lanes
 //    start a candidate, run in FP32 with rigorous rounding margins and fall
 //    back to FP64 only inside the margin, so every decision equals the FP64
@@ -108,14 +108,17 @@ __device__ __forceinline__ void group_fetch(const Work& w, unsigned long long& s
 }
 
 // Shared memory of one CTA of the FP64 lane loop: the t-basis slabs, the
-// beta term's per-thread entries and per-warp scratch, the GLL
-// differentiation matrix and the CTA's point counter.
+// beta term's per-thread entries and per-warp scratch, the node start's
+// entries of G and table of starting lanes, the GLL differentiation matrix
+// and the CTA's point counter.
 template <int N, int D, int DR>
 struct F64Shared {
   double slab[DR == 3 ? 2 * N * kFindThreads : 1];
   double hs[beta_entries<DR>() * kFindThreads];
   double bscr[(kFindThreads / 32) * kBetaScratch];
+  double sg[D * DR * kFindThreads];  // node start: G of the starting lanes
   double dn[N * N];
+  int sl[kFindThreads];              // node start: starting lanes by rank
   unsigned long long next;
 };
 
@@ -300,10 +303,10 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
       if (start) rel_point<D>(*mp, e, xs, xr);
       int nb = 0;
       closest_node_warp<N, D, DR>(start, *mp, e, xs, xr, nb);
+      double xv[D];
+      node_start_warp<N, D, DR>(start, *mp, e, nb, s_dn, sh.sg, sh.sl, xv, G);
       if (start) {
         node_coords<N, DR>(B, nb, r);
-        double xv[D];
-        node_start<N, D, DR>(*mp, e, nb, s_dn, xv, G);
         F = 0.0;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
