@@ -135,7 +135,11 @@ int fp_findpts(fp_mesh m, const double* pts_dev, int64_t n, int32_t* code,
  * FP_NSTATS uint64 values, caller-zeroed):
  *   [0] candidates that passed the box filter  [1] Newton iterations
  *   [2] rejected trust-region steps            [3] Newton steps with beta = 1
- *   [4] FP64 refinement evaluations (mixed)    [5] box tests decided in FP64
+ *   [4] FP64 refinement evaluations (mixed path's FP32 kernel); in the FP64
+ *       kernel, the iterations ended by a certified last step (volumes: the
+ *       next step is bounded below the rounding noise, so the sub-tolerance
+ *       step that Sec. 3.2.1 would take after one more evaluation is left out)
+ *                                              [5] box tests decided in FP64
  *   [6] points the mixed path handed to its FP64 kernel
  *   [7] full evaluations of x(r) and G(r), re-evaluations after a rejected
  *       step not counted: in the FP64 kernel one per trial step (a
@@ -422,6 +426,17 @@ int fp_get_info(fp_mesh m, fp_mesh_info* info);
  * obb_c[NE][d] the OBB centre; obb_A[NE][d][d] (row-major) the map A with
  * |A (x - c)|_inf <= 1 exactly on the expanded OBB.  Synchronous. */
 int fp_get_boxes(fp_mesh m, double* aabb, double* obb_c, double* obb_A, void* stream);
+
+/* Copies each element's curvature bound into curv_dev[NE] (device, FP64).
+ * The paper has no counterpart: the find kernels use it to certify that a
+ * Newton step is the last one needed (the next step, bounded from the
+ * linear model's residual and this term, is far below the tolerance).
+ * Volumes (d == dr): L_e >= max over element e of sum_jk |d2 x_c / dr_j dr_k|
+ * for every component c (the second derivatives' values at the GLL nodes
+ * through the Lebesgue constant), as stored for the kernels (FP32, widened
+ * by 1e-6); 0 for surfaces and lines.  Synchronous.
+ * Errors: FP_EINVAL, FP_ELAUNCH. */
+int fp_get_curvature(fp_mesh m, double* curv_dev, void* stream);
 
 /* Copies Psi_L in CSR form into caller device buffers: cell_start[n_cells+1],
  * cell_elems[n_cell_entries], element ids ascending within a cell.  Cell

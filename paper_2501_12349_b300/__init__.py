@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             "fp_get_info": ([_vp, ctypes.POINTER(FpMeshInfo)], _int),
             "fp_get_boxes": ([_vp, _vp, _vp, _vp, _vp], _int),
             "fp_get_grid": ([_vp, _vp, _vp, _vp], _int),
+            "fp_get_curvature": ([_vp, _vp, _vp], _int),
             "fp_device_status": ([_vp, ctypes.POINTER(_int), _vp], _int),
             "fp_status_string": ([_int], ctypes.c_char_p),
             "fp_alu_peak": ([_int, _int, ctypes.POINTER(ctypes.c_double), _vp], _int),
@@ -247,6 +248,11 @@ def fp_get_boxes(mesh, aabb, obb_c, obb_A, stream=None) -> None:
     import torch
     _check("fp_get_boxes", lib().fp_get_boxes(mesh, _ptr(aabb, torch.float64), _ptr(obb_c, torch.float64),
                                               _ptr(obb_A, torch.float64), _stream(stream)))
+
+
+def fp_get_curvature(mesh, curv, stream=None) -> None:
+    import torch
+    _check("fp_get_curvature", lib().fp_get_curvature(mesh, _ptr(curv, torch.float64, "curv"), _stream(stream)))
 
 
 def fp_get_grid(mesh, cell_start, cell_elems, stream=None) -> None:
@@ -643,6 +649,13 @@ class Mesh:
         oA = torch.empty((self.NE, self.d, self.d), dtype=torch.float64, device=dev)
         fp_get_boxes(self.handle, aabb, oc, oA)
         return aabb, oc, oA
+
+    def curvature(self):
+        """Per-element curvature bounds (fp_get_curvature), [NE] FP64 on the device."""
+        import torch
+        curv = torch.empty(self.NE, dtype=torch.float64, device="cuda")
+        fp_get_curvature(self.handle, curv)
+        return curv
 
     def grid(self):
         import torch

@@ -667,6 +667,105 @@ __device__ __forceinline__ T model_dist2(const T (&G)[D * DR], const T (&dx)[D],
   return f;
 }
 
+// Certified stop of the FP64 iteration (volumes, D == DR).  The iteration
+// of Sec. 3.2.1 stops once its proposed step is below the Newton tolerance;
+// the full evaluation of x and G after the step before it serves only to
+// compute that last, sub-tolerance step.  Here the next step is bounded
+// instead, from quantities at hand, and the iteration stops at r' = r + s
+// when the bound leaves nothing the last step would still correct:
+//   * the exact residual at r' is e' = (dx - G s) - R, |R|_inf <= L |s|^2 / 2
+//     with L the element's bound on sum_jk |d2 x_c / dr_j dr_k| (setup:
+//     DevMesh::curv); dx - G s is the linear model's residual t, computed
+//     here with rounding <= 4u (|dx| + |G| |s|), and dx itself carries the
+//     evaluation's rounding, covered by 1e-14 X (X the element's coordinate
+//     scale);
+//   * |G(r')^-1|_inf <= g / (1 - g L |s|), g = |G^-1|_inf (adjugate / det,
+//     widened by 1e-6 for its own rounding), by the Banach lemma, since
+//     |G(r') - G(r)|_inf <= L |s|;
+//   * so with q = g L |s| < 1 the next step, and the distance from r' to the
+//     root the iteration converges to (the later steps shrink
+//     quadratically), are at most g (|t| + slack + L |s|^2 / 2) / (1 - q)
+//     (1 + q'), q' tiny (covered by the widening of g).
+// Certified when (a) that bound without the evaluation's rounding is at
+// most kF64CertModel: the stop then moves r by no more than the rounding
+// noise the full iteration's last step carries as well, so r, dist2 and the
+// interpolated values agree with the full iteration's to its own accuracy;
+// (b) the whole bound is at most kF64CertStep (half the tolerance); and
+// (c) every |r'_j| < 1 - kCertEdge, so the code (INTERIOR) is the full
+// iteration's.  Both tests are done without a division, as
+// g_num (num + k L |s|) <= k |det|.  On success the step is taken and dist2
+// is the model value |t|^2, as for a sub-tolerance step.  The caller passes
+// only unclipped, beta-free steps of an iterate off the element boundary.
+constexpr double kF64CertModel = 2e-15;
+constexpr double kF64CertStep = 5e-11;
+constexpr double kCertEdge = 1e-10;
+constexpr double kCertMaxStep = 1e-4;  // larger steps are not tried (g L |s|^2 >> kF64CertModel on curved elements)
+
+template <int D>
+__device__ __forceinline__ bool certified_stop(const double (&G)[D * D], const double (&dx)[D], const double (&ds)[D],
+                                               const double (&rn)[D], double mx, float curv, double xscale,
+                                               double& F) {
+  using FB = FBits<double>;
+  // |r'_j| < 1 - kCertEdge, on the bit patterns
+  constexpr long long kEdge = 0x3feffffffff24190LL;  // the bits of 1 - kCertEdge (0.9999999999)
+  bool in = true;
+#pragma unroll
+  for (int j = 0; j < D; ++j) in &= (FB::of(rn[j]) & FB::kAbs) < kEdge;
+  if (!in) return false;
+  // adjugate of G (row-major, G[c * D + j]), det, row sums of |adj| and |G|
+  double adj[D * D], det;
+  if constexpr (D == 2) {
+    adj[0] = G[3];
+    adj[1] = -G[1];
+    adj[2] = -G[2];
+    adj[3] = G[0];
+    det = G[0] * G[3] - G[1] * G[2];
+  } else {
+    adj[0] = G[4] * G[8] - G[5] * G[7];
+    adj[1] = G[2] * G[7] - G[1] * G[8];
+    adj[2] = G[1] * G[5] - G[2] * G[4];
+    adj[3] = G[5] * G[6] - G[3] * G[8];
+    adj[4] = G[0] * G[8] - G[2] * G[6];
+    adj[5] = G[2] * G[3] - G[0] * G[5];
+    adj[6] = G[3] * G[7] - G[4] * G[6];
+    adj[7] = G[1] * G[6] - G[0] * G[7];
+    adj[8] = G[0] * G[4] - G[1] * G[3];
+    det = G[0] * adj[0] + G[1] * adj[3] + G[2] * adj[6];
+  }
+  long long arow = 0, grow = 0, tmax = 0, dmax = 0;
+  double t[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double a = 0.0, b = 0.0, ti = dx[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      a += fabs(adj[i * D + j]);
+      b += fabs(G[i * D + j]);
+      ti = fma(-G[i * D + j], ds[j], ti);
+    }
+    t[i] = ti;
+    arow = max(arow, FB::of(a));
+    grow = max(grow, FB::of(b));
+    tmax = max(tmax, FB::of(ti) & FB::kAbs);
+    dmax = max(dmax, FB::of(dx[i]) & FB::kAbs);
+  }
+  const double adet = fabs(det);
+  const double an = FB::from(arow) * (1.0 + 1e-6);  // g = an / adet
+  const double L = (double)curv;
+  const double Ls = L * mx;
+  constexpr double u4 = 4.0 * 1.1102230246251565e-16;
+  const double num = FB::from(tmax) + fma(u4, fma(FB::from(grow), mx, FB::from(dmax)), 0.5 * Ls * mx);
+  // g num / (1 - q) <= k with g = an / |det|, q = g L |s| (which the
+  // inequalities also hold below 1)
+  if (!(an * fma(kF64CertModel, Ls, num) <= kF64CertModel * adet)) return false;
+  if (!(an * fma(kF64CertStep, Ls, fma(1e-14, xscale, num)) <= kF64CertStep * adet)) return false;
+  double f = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) f = fma(t[c], t[c], f);
+  F = f;
+  return true;
+}
+
 // Ratio test of Sec. 3.2.1 with the rounding-level acceptance; updates alpha.
 template <typename T>
 __device__ __forceinline__ bool trial_accepts(T F, T Fn, T pred, bool clipped, T xscale, T& alpha,

@@ -249,9 +249,16 @@ __device__ __forceinline__ void find_f64_loop(const Work& w, const BasisTab& B, 
           double ds[DR];
           bool used_beta;
           const double mx = newton_step<D, DR>(G, dx, r, alpha, beta, HS, rn, ds, clipped, used_beta);
-          if (below_nonneg(mx, mp->newton_tol)) {
-            // the last step is taken; dist2 from the linear model at r
-            F = model_dist2<D, DR>(G, dx, ds);
+          bool stop = below_nonneg(mx, mp->newton_tol);
+          if (stop) F = model_dist2<D, DR>(G, dx, ds);  // dist2 from the linear model at r
+          if constexpr (DR == D) {
+            // volumes: the step before the last one can be certified
+            if (!stop && !beta && !clipped && below_nonneg(mx, kCertMaxStep)) {
+              stop = certified_stop<D>(G, dx, ds, rn, mx, __ldg(mp->curv + e), xscale, F);
+              if (stop) ++cnt.v[4];
+            }
+          }
+          if (stop) {  // the step is taken
 #pragma unroll
             for (int j = 0; j < DR; ++j) r[j] = rn[j];
             ++cnt.v[1];

@@ -43,7 +43,8 @@ constexpr int kPark = 31;          // run the FP64 refinement with >= kPark lane
 constexpr int kMaxRefine = 4;
 constexpr double kCertStep = 2e-11;  // volumes: accept the first FP64 correction when the
                                      // next step is estimated below this (see certified)
-constexpr double kCertEdge = 1e-10;  // ... and the result is this far inside the element
+                                     // and the result is kCertEdge (find_common.cuh)
+                                     // inside the element
 
 // The FP64 kernel that finishes the queued points counts into the second
 // half of the statistics array, so the two precisions' work stays separate.

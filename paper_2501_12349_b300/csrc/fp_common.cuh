@@ -72,6 +72,8 @@ struct DevMesh {
   const double* obb_A;     // [NE][d][d]
   const float* box32;      // [NE][BOX32]: FP32 copy of aabb, obb_c, obb_A and the
                            // coordinate scale X (max |aabb|), for certified FP32 tests
+  const float* curv;       // [NE] volumes: bound of sum_jk |d2 x_c / dr_j dr_k| over the element
+                           // (the FP64 kernel's certified stop); 0 for surfaces and lines
   const int* cell_start;   // [ncell + 1]
   const int* cell_elems;   // [nnz]
   int64_t NE;
@@ -146,6 +148,7 @@ struct fp_mesh_s {
   double* obb_c;
   double* obb_A;
   float* box32;
+  float* curv;
   int* cell_start;
   int* cell_elems;
   int* status;

@@ -134,11 +134,8 @@ namespace {
 
 // Sums of |phi_i^(k)(r)| over the N Lagrange bases, maximised over r in
 // [-1, 1] by dense sampling (20001 points, 2% added for the sampling), for
-// k = 0, 1, 2; from them the factor K such that, for an element whose nodal
-// values deviate by at most dev from an affine function of r, every second
-// derivative sum over (j, k) of |d^2 x_c / dr_j dr_k| is at most dev * K:
-// dr * L2 L0^(dr-1) (j = k) + dr (dr - 1) * L1^2 L0^(dr-2) (j != k).
-double curvature_factor(int N, int dr) {
+// k = 0, 1, 2 (Ls[0] is the Lebesgue constant of the nodes).
+void basis_sums(int N, double Ls[3]) {
   double z[FP_MAX_N], wq[FP_MAX_N], w[FP_MAX_N];
   gll_host(N, z, wq);
   for (int i = 0; i < N; ++i) {
@@ -147,7 +144,7 @@ double curvature_factor(int N, int dr) {
       if (m != i) p *= (z[i] - z[m]);
     w[i] = 1.0 / p;
   }
-  double L[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < 3; ++q) Ls[q] = 0.0;
   const int S = 20001;
   for (int k = 0; k < S; ++k) {
     const double x = -1.0 + 2.0 * k / (S - 1);
@@ -166,9 +163,20 @@ double curvature_factor(int N, int dr) {
       a[1] += fabs(w[i] * dp);
       a[2] += fabs(w[i] * d2p);
     }
-    for (int q = 0; q < 3; ++q) L[q] = std::max(L[q], a[q]);
+    for (int q = 0; q < 3; ++q) Ls[q] = std::max(Ls[q], a[q]);
   }
-  for (double& v : L) v *= 1.02;
+  for (int q = 0; q < 3; ++q) Ls[q] *= 1.02;
+}
+
+// The factor K such that, for an element whose nodal values deviate by at
+// most dev from an affine function of r, every second-derivative sum over
+// (j, k) of |d^2 x_c / dr_j dr_k| is at most dev * K:
+// dr * L2 L0^(dr-1) (j = k) + dr (dr - 1) * L1^2 L0^(dr-2) (j != k).  This
+// cruder bound serves the mixed path's certified refinement, whose
+// acceptance threshold was chosen with it.
+double curvature_factor(int N, int dr) {
+  double L[3];
+  basis_sums(N, L);
   const double pure = L[2] * pow(L[0], dr - 1), mixed = dr > 1 ? L[1] * L[1] * pow(L[0], dr - 2) : 0.0;
   return dr * pure + dr * (dr - 1) * mixed;
 }
@@ -757,6 +765,89 @@ __global__ void k_coords32(const double* __restrict__ x, const double* __restric
 // pad xc[3] T[3][3], rounded to nearest (the certified FP32 tests carry
 // their own margins); Xrel = largest AABB half-width, slightly enlarged,
 // bounds |x - x_ref| over the element; xc = x(0) - x_ref; T the OBB frame.
+// Volumes: the element's bound L >= max over the element of
+// sum_jk |d^2 x_c / dr_j dr_k| for every component c (the curvature term of
+// the FP64 kernel's certified stop).  Each second derivative of x_c
+// is a polynomial of degree < N in every direction, so its values at the
+// GLL nodes, obtained exactly (up to rounding) by applying the GLL
+// differentiation matrix dn along r_j and then along r_k, bound it on the
+// whole element through the Lebesgue constant: |d_jk x_c| <= Lambda^dr
+// max_nodes |d_jk x_c|.  The rounding of the two N-term sums is covered by
+// an absolute slack, rslack max_n |x_c| (rslack = 2N u S^2 Lambda^dr dr^2,
+// S the largest absolute row sum of dn).  One CTA per element, one component
+// at a time: x_c, then its first derivatives along each r_j, in shared
+// memory.
+template <int N, int D>
+__global__ void __launch_bounds__(kBoxThreads)
+    k_curvature(const double* __restrict__ coords, int64_t NE, BasisTab B, double lam_dr, double rslack,
+                float* __restrict__ curv) {
+  constexpr int NN = ipow(N, D);
+  constexpr int NPAIR = D * (D + 1) / 2;
+  __shared__ double xs[NN];
+  __shared__ double g1[D][NN];
+  __shared__ double red[kBoxThreads / 32][NPAIR + 1];
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  const int st[3] = {1, N, N * N};
+  double Lmax = 0.0;
+  for (int c = 0; c < D; ++c) {
+    for (int n = tid; n < NN; n += blockDim.x) xs[n] = coords[((int64_t)c * NE + e) * NN + n];
+    __syncthreads();
+    for (int idx = tid; idx < D * NN; idx += blockDim.x) {
+      const int j = idx / NN, n = idx % NN;
+      const int ij = (n / st[j]) % N;
+      const double* line = xs + (n - ij * st[j]);
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) s = fma(B.dn[ij * N + m], line[m * st[j]], s);
+      g1[j][n] = s;
+    }
+    __syncthreads();
+    double mxv[NPAIR + 1];
+#pragma unroll
+    for (int q = 0; q <= NPAIR; ++q) mxv[q] = 0.0;
+    for (int n = tid; n < NN; n += blockDim.x) {
+      mxv[NPAIR] = fmax(mxv[NPAIR], fabs(xs[n]));
+      int q = 0;
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int k = j; k < D; ++k, ++q) {
+          const int ik = (n / st[k]) % N;
+          const double* line = &g1[j][n - ik * st[k]];
+          double s = 0.0;
+#pragma unroll
+          for (int m = 0; m < N; ++m) s = fma(B.dn[ik * N + m], line[m * st[k]], s);
+          mxv[q] = fmax(mxv[q], fabs(s));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q <= NPAIR; ++q) {
+      double v = mxv[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((tid & 31) == 0) red[tid >> 5][q] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double Lc = 0.0;
+      int q = 0;
+      for (int j = 0; j < D; ++j)
+        for (int k = j; k < D; ++k, ++q) {
+          double v = red[0][q];
+          for (int w = 1; w < kBoxThreads / 32; ++w) v = fmax(v, red[w][q]);
+          Lc += (j == k ? 1.0 : 2.0) * v;
+        }
+      double xm = red[0][NPAIR];
+      for (int w = 1; w < kBoxThreads / 32; ++w) xm = fmax(xm, red[w][NPAIR]);
+      Lmax = fmax(Lmax, lam_dr * Lc + rslack * xm);
+    }
+    __syncthreads();
+  }
+  // rounded to FP32 upwards by the widening (FP32 rounding is below 1e-7)
+  if (tid == 0) curv[e] = (float)(Lmax * (1.0 + 1e-6));
+}
+
 __global__ void k_box32(const double* __restrict__ aabb, const double* __restrict__ obb_c,
                         const double* __restrict__ obb_A, const double* __restrict__ lin, int64_t NE,
                         int d, float* __restrict__ out) {
@@ -802,6 +893,7 @@ void free_mesh_memory(fp_mesh_s* m) {
   cudaFree(m->obb_c);
   cudaFree(m->obb_A);
   cudaFree(m->box32);
+  cudaFree(m->curv);
   cudaFree(m->cell_start);
   cudaFree(m->cell_elems);
   cudaFree(m->status);
@@ -820,6 +912,7 @@ fp::DevMesh fp_mesh_s::view() const {
   v.obb_c = obb_c;
   v.obb_A = obb_A;
   v.box32 = box32;
+  v.curv = curv;
   v.cell_start = cell_start;
   v.cell_elems = cell_elems;
   v.NE = NE;
@@ -871,6 +964,30 @@ int build_boxes_and_grid(fp_mesh_s* m, cudaStream_t st) {
     });
     if (rc != FP_OK) break;
     if (timed) cudaEventRecord(ev[1], st);
+    // volumes: the curvature bound of the FP64 certified stop (after the timed k_boxes)
+    if (m->d == m->dr) {
+      double Ls[3];
+      basis_sums(m->N, Ls);
+      const double lam = Ls[0];
+      double S = 0.0;
+      for (int i = 0; i < m->N; ++i) {
+        double a = 0.0;
+        for (int k = 0; k < m->N; ++k) a += fabs(m->basis.dn[i * m->N + k]);
+        S = std::max(S, a);
+      }
+      const double lam_dr = pow(lam, m->dr);
+      const double rslack = 2.0 * m->N * 1.1102230246251565e-16 * S * S * lam_dr * m->dr * m->dr;
+      rc = dispatch_shape(m->N, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+        constexpr int N = decltype(Nc)::value, D = decltype(Dc)::value, DR = decltype(DRc)::value;
+        if constexpr (D == DR) {
+          k_curvature<N, D><<<(unsigned)m->NE, kBoxThreads, 0, st>>>(m->coords, m->NE, m->basis, lam_dr,
+                                                                     rslack, m->curv);
+          return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+        }
+        return FP_OK;
+      });
+      if (rc != FP_OK) break;
+    }
     // grid bounds = union of the expanded AABBs
     double* dbounds = nullptr;
     if (cudaMalloc(&dbounds, 6 * sizeof(double)) != cudaSuccess) {
@@ -1046,7 +1163,9 @@ extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int6
     if ((rc = dev_alloc(&m->obb_c, (size_t)NE * d, &m->bytes)) != FP_OK) break;
     if ((rc = dev_alloc(&m->obb_A, (size_t)NE * d * d, &m->bytes)) != FP_OK) break;
     if ((rc = dev_alloc(&m->status, 1, &m->bytes)) != FP_OK) break;
+    if ((rc = dev_alloc(&m->curv, (size_t)NE, &m->bytes)) != FP_OK) break;
     if (cudaMemsetAsync(m->status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(m->curv, 0, (size_t)NE * sizeof(float), st) != cudaSuccess ||
         cudaMemcpyAsync(m->coords, coords_dev, nc * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
             cudaSuccess) {
       rc = FP_ELAUNCH;
@@ -1109,6 +1228,22 @@ extern "C" int fp_get_boxes(fp_mesh m, double* aabb, double* obb_c, double* obb_
   if (aabb) FP_CUDA_TRY(cudaMemcpyAsync(aabb, m->aabb, m->NE * 2 * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (obb_c) FP_CUDA_TRY(cudaMemcpyAsync(obb_c, m->obb_c, m->NE * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (obb_A) FP_CUDA_TRY(cudaMemcpyAsync(obb_A, m->obb_A, m->NE * d * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  FP_CUDA_TRY(cudaStreamSynchronize(st));
+  return FP_OK;
+}
+
+namespace {
+__global__ void k_get_curvature(const float* __restrict__ curv, int64_t NE, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < NE; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (double)curv[e];
+}
+}  // namespace
+
+extern "C" int fp_get_curvature(fp_mesh m, double* curv_dev, void* stream) {
+  if (!m || !curv_dev) return FP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_get_curvature<<<fp::grid_for(m->NE, 256, 148 * 8), 256, 0, st>>>(m->curv, m->NE, curv_dev);
+  FP_CUDA_TRY(cudaGetLastError());
   FP_CUDA_TRY(cudaStreamSynchronize(st));
   return FP_OK;
 }

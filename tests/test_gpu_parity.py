@@ -224,6 +224,46 @@ def test_edge_cases(fp, torch):
     m.close()
 
 
+@pytest.mark.parametrize("case", ["quad2d_p3", "hex3d_p4", "hex3d_p6_strong"])
+def test_curvature_bound(fp, torch, case):
+    """The per-element curvature bound behind the certified stops of the find
+    kernels bounds the map's second derivatives, sum_jk |d2 x_c / dr_j dr_k|,
+    at dense samples of the element (second derivatives from the oracle's
+    Lagrange basis and its derivatives), and is no more than 30x above them."""
+    if case == "hex3d_p6_strong":
+        coords, d, dr, order = W.hex_mesh(4, 6, 0.6), 3, 3, 6
+    else:
+        coords, d, dr, order, _ = CASES[case]()
+    N = order + 1
+    m = gpu_mesh(fp, torch, coords, d, dr, order)
+    L = to_np(m.curvature())
+    X = np.asarray(coords).reshape(d, -1, N ** dr)
+    rng = np.random.default_rng(5)
+    els = rng.choice(X.shape[1], size=min(12, X.shape[1]), replace=False)
+    tabs = [oracle.lagrange(N, r) for r in np.linspace(-1, 1, 9)]
+    P, D1, D2 = (np.array([t[q] for t in tabs]) for q in range(3))  # [sample][basis]
+    for e in els:
+        worst = 0.0
+        for c in range(d):
+            if dr == 3:
+                U = X[c, e].reshape(N, N, N)  # [k][j][i], i along r_0
+
+                def sec(A0, A1, A2):
+                    return np.abs(np.einsum("kji,ai,bj,gk->abg", U, A0, A1, A2))
+                s = (sec(D2, P, P) + sec(P, D2, P) + sec(P, P, D2)
+                     + 2 * (sec(D1, D1, P) + sec(D1, P, D1) + sec(P, D1, D1)))
+            else:
+                U = X[c, e].reshape(N, N)  # [j][i]
+
+                def sec(A0, A1):
+                    return np.abs(np.einsum("ji,ai,bj->ab", U, A0, A1))
+                s = sec(D2, P) + sec(P, D2) + 2 * sec(D1, D1)
+            worst = max(worst, float(s.max()))
+        assert worst <= L[e], (case, e, worst, L[e])
+        assert L[e] <= 30 * worst + 1e-12, (case, e, worst, L[e])
+    m.close()
+
+
 def test_stats_counters(fp, torch):
     w = W.hex_config(13, 5000, 1, n=6)
     om = oracle.OracleMesh(w.coords, 3, 3, w.N)
@@ -234,7 +274,11 @@ def test_stats_counters(fp, torch):
     os_ = np.zeros(8, np.int64)
     om.findpts(w.pts, stats=os_)
     assert gs[0] == os_[0]                       # candidates: exact
-    assert abs(gs[1] - os_[1]) <= 0.01 * os_[1]  # iterations: same algorithm
+    # iterations: the same algorithm, except that a certified stop (volumes)
+    # ends an iteration one step before the sub-tolerance step the oracle
+    # takes, so each one [4] accounts for exactly one oracle iteration
+    assert gs[4] > 0.3 * gs[0]
+    assert abs(gs[1] + gs[4] - os_[1]) <= 0.01 * os_[1]
     m.close()
 
 
