@@ -50,11 +50,11 @@ KERNEL_SOURCES = {
                      "fp_common.cuh", "find.cu", "order.cu"],
 }
 TRAFFIC = {
-    # ncu --set full -k regex:k_find_f64 -s 3 -c 1 on
+    # ncu -k regex:k_find_f64 -s 3 -c 1 (sections SpeedOfLight, MemoryWorkloadAnalysis, ...) on
     # bench.py --steps 2 --warmup 3 --skip-mixed --skip-batch --skip-serve --no-cpu-baseline
-    "k_find_f64": {"sha": "7baa73604ffe6efd", "bytes": 721328128 + 73786624},
+    "k_find_f64": {"sha": "e2f0f3935c7f7ba1", "bytes": 727892224 + 74420480},
     # the same with --precision mixed and -k regex:k_find_mixed
-    "k_find_mixed": {"sha": "c19ac5211d96ac84", "bytes": 538218240 + 69063680},
+    "k_find_mixed": {"sha": "b0ba1add4990d042", "bytes": 535060736 + 68683008},
 }
 
 
