@@ -182,7 +182,15 @@ int fp_findpts_mixed_noalloc(fp_mesh m, const double* pts_dev, int64_t n, int32_
 /* Interpolate (Sec. 3.3): out[c][p] = u_c(r_p) in element elem_p for the
  * nc components of field_dev ([nc][NE][N^dr] FP64, device, same node layout
  * as the coordinates); 0 where code == FP_NOT_FOUND.  The same find output
- * serves any number of fields.  Errors: FP_EINVAL, FP_ELAUNCH. */
+ * serves any number of fields.
+ * Precision follows the mesh's setting (fp_set_precision): FP_F64 contracts
+ * in FP64; FP_MIXED contracts in double-float arithmetic on the FP32 pipe
+ * (pairs of FP32 values with error-free transformations), within about
+ * 1e-13 of the element's nodal scale of the FP64 result, and then takes
+ * 8 bytes of device scratch per field value from the stream-ordered
+ * allocator for the duration of the call (the field split into those
+ * pairs after an exact power-of-two scaling per component).
+ * Errors: FP_EINVAL, FP_ENOMEM (FP_MIXED scratch), FP_ELAUNCH. */
 int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
             int64_t n, const double* field_dev, int nc, double* out, void* stream);
 
@@ -197,7 +205,8 @@ int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r
  *   not NULL, out_host [nc][n] as fp_eval.  All host buffers should be
  *   pinned (page-locked), or the copies do not overlap the kernels.
  * Device scratch: (8 (d + dr + 1 + nc) + 8) bytes per point, plus the cell
- * order's, from the stream-ordered allocator for the duration of the call.
+ * order's and, with FP_MIXED and a field, fp_eval's, from the stream-ordered
+ * allocator for the duration of the call.
  * Synchronous: returns when the results are in host memory.
  * Errors: FP_EINVAL, FP_ENOMEM, FP_ELAUNCH. */
 int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int32_t* code_host,
@@ -210,7 +219,8 @@ int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int32_t* code_
  * field_dev is [nc][NE][(field_order+1)^dr] FP64 on the GLL nodes of
  * field_order + 1 points per direction, in the node layout of the
  * coordinates; code, elem, r come from fp_findpts on the same mesh and
- * out[c][p] as fp_eval.  field_order == the mesh's order is fp_eval.
+ * out[c][p] as fp_eval (precision and scratch as there).  field_order ==
+ * the mesh's order is fp_eval.
  * Errors: FP_EINVAL; FP_EUNSUPPORTED unless 1 <= field_order <= 7;
  * FP_ELAUNCH. */
 int fp_eval_order(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,

@@ -1,18 +1,22 @@
 // Interpolate (Sec. 3.3, Eq. u_tensor): u(r*) in element e* for each found
 // point, one thread per point, the contraction sum-factorised (N^3 + N^2 + N
-// FMA per component for a hex).  FP64-pipe bound like find.
+// FMA per component for a hex).  FP64-pipe bound like find; with the mesh in
+// mixed precision, the same contraction in double-float arithmetic on the
+// FP32 pipe (below).
 //
 // The field's nodes per direction, N~, may differ from the mesh's N (Sec. 2,
 // after Eq. u_tensor: a solution is often represented at another order than
 // the coordinates); the kernel is the same with the GLL basis of N~ points.
 #include <mutex>
 
+#include "df64.cuh"
 #include "fp_basis.cuh"
 #include "fp_common.cuh"
 
 namespace fp {
 
 constexpr int kEvalThreads = 128;
+constexpr int64_t kEvalOrderMin = 16384;  // FP_MIXED: element order from this many points
 
 template <int N, int DR>
 __global__ void __launch_bounds__(kEvalThreads)
@@ -41,6 +45,142 @@ __global__ void __launch_bounds__(kEvalThreads)
   }
 }
 
+// ---- FP_MIXED: the contraction in double-float arithmetic -----------------
+//
+// With the mesh in mixed precision, interpolation runs on the FP32 pipe: the
+// field, scaled per component by an exact power of two so that its largest
+// magnitude lies in [1, 2), is split once per call into double-float pairs
+// (k_field_split), the bases are evaluated in double-float arithmetic from
+// the split r, and each stage of the sum-factorised contraction is a
+// compensated dot product of N terms (DfAcc).  Error: the input splits and
+// each double-float operation contribute about 2^-48 relative, each N-term
+// compensated sum at most about N u^2 of its sum of |terms| (u = 2^-24), so
+// |u_df - u| <= about 1e-13 of the element's nodal scale (at N <= 8, with the
+// Lebesgue constant's growth over the three stages), against the 1e-12 of
+// the interpolation tolerance; in practice a few 1e-16.
+
+// Per component c: the largest biased exponent of |field| (atomicMax).
+__global__ void k_field_exp(const double* __restrict__ field, int64_t per, int* __restrict__ emax) {
+  const int c = blockIdx.y;
+  const double* f = field + (int64_t)c * per;
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)((__double_as_longlong(f[i]) >> 52) & 0x7ff));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(emax + c, m);
+}
+
+// 2^(1023 - e) for a biased exponent e in [1, 2046], else 1 (an all-zero
+// component, or one holding an infinity or NaN, which propagates as in FP64).
+__device__ __forceinline__ double unscale_of(int e) {
+  return (e >= 1 && e <= 2046) ? __longlong_as_double((long long)(2046 - e) << 52) : 1.0;
+}
+__device__ __forceinline__ double scale_of(int e) {
+  return (e >= 1 && e <= 2046) ? __longlong_as_double((long long)e << 52) : 1.0;
+}
+
+// The field as (hi, lo) pairs, one 8-byte load per value as in FP64.
+__global__ void k_field_split(const double* __restrict__ field, int64_t per, const int* __restrict__ emax,
+                              float2* __restrict__ fs) {
+  const int c = blockIdx.y;
+  const double s = unscale_of(emax[c]);
+  const int64_t o = (int64_t)c * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
+    const df v = df_from(field[o + i] * s);  // exact scaling by a power of two
+    fs[o + i] = make_float2(v.h, v.l);
+  }
+}
+
+// Points in element order for the double-float contraction: counts per
+// element (bucket NE for the points not found), an exclusive scan, then
+// each point placed in its element's range (order within an element
+// arbitrary: every point's value is computed on its own).  The lanes of a
+// warp then read the same element's values, where in the given order each
+// lane's gather is a cache line of its own.
+__global__ void k_elem_count(const int* __restrict__ code, const int* __restrict__ elem, int64_t n, int64_t NE,
+                             int* __restrict__ counts) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int e = __ldg(elem + p);
+    const int64_t b = (__ldg(code + p) != FP_NOT_FOUND && e >= 0 && e < NE) ? e : NE;
+    atomicAdd(counts + b, 1);
+  }
+}
+
+__global__ void k_elem_scatter(const int* __restrict__ code, const int* __restrict__ elem, int64_t n, int64_t NE,
+                               int* __restrict__ next, int* __restrict__ perm) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int e = __ldg(elem + p);
+    const int64_t b = (__ldg(code + p) != FP_NOT_FOUND && e >= 0 && e < NE) ? e : NE;
+    perm[atomicAdd(next + b, 1)] = (int)p;
+  }
+}
+
+template <int N, int DR>
+__global__ void __launch_bounds__(kEvalThreads)
+    k_eval_df(const BasisTab B, const int* __restrict__ code, const int* __restrict__ elem,
+              const double* __restrict__ r, int64_t n, const int* __restrict__ perm,
+              const float2* __restrict__ fs, const int* __restrict__ emax, int nc, int64_t NE,
+              double* __restrict__ out, int* status) {
+  constexpr int NN = ipow(N, DR);
+  const int64_t cs = NE * NN;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = perm ? (int64_t)__ldg(perm + t) : t;
+    const int c0 = __ldg(code + p), e = __ldg(elem + p);
+    const bool valid = c0 != FP_NOT_FOUND && e >= 0 && e < NE;
+    if (c0 != FP_NOT_FOUND && !valid) record_status(status, FP_DEV_BAD_ELEM);
+    if (!valid) {
+      for (int c = 0; c < nc; ++c) out[(int64_t)c * n + p] = 0.0;
+      continue;
+    }
+    df ph[DR][N];
+#pragma unroll
+    for (int j = 0; j < DR; ++j) lagrange_sym_values_df<N>(B, df_from(__ldg(r + p * DR + j)), ph[j]);
+    for (int c = 0; c < nc; ++c) {
+      const float2* x = fs + c * cs + (int64_t)e * NN;
+      auto ld = [&](int q) {
+        const float2 v = __ldg(x + q);
+        return df{v.x, v.y};
+      };
+      DfAcc acc;
+      if constexpr (DR == 3) {
+#pragma unroll 1
+        for (int k = 0; k < N; ++k) {
+          df pk = ph[2][0];
+#pragma unroll
+          for (int q = 1; q < N; ++q)
+            if (q == k) pk = ph[2][q];
+          DfAcc bk;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            DfAcc a;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              const int q = (k * N + j) * N + i;
+              a.add(ld(q), ph[0][i]);
+            }
+            bk.add(a.get(), ph[1][j]);
+          }
+          acc.add(bk.get(), pk);
+        }
+      } else if constexpr (DR == 2) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          DfAcc a;
+#pragma unroll
+          for (int i = 0; i < N; ++i) a.add(ld(j * N + i), ph[0][i]);
+          acc.add(a.get(), ph[1][j]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc.add(ld(i), ph[0][i]);
+      }
+      out[(int64_t)c * n + p] = df_to(acc.get()) * scale_of(__ldg(emax + c));
+    }
+  }
+}
+
 }  // namespace fp
 
 namespace {
@@ -65,14 +205,55 @@ int eval_impl(fp_mesh m, const int32_t* code, const int32_t* elem, const double*
   if (!code || !elem || !r || !field || !out) return FP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t t0 = timer_mark(m, st);
-  const int rc = dispatch_shape(Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
-    constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;
-    (void)Dc;
-    const int blocks = grid_for(n, kEvalThreads, 148 * 64);
-    k_eval_f64<N, DR><<<blocks, kEvalThreads, 0, st>>>(*B, code, elem, r, n, field, nc, m->NE, out,
-                                                        m->status);
-    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
-  });
+  int rc = FP_OK;
+  if (m->precision == FP_MIXED) {
+    // scratch: the split field (a float pair per value), the exponents and,
+    // for calls of kEvalOrderMin points or more, the element order
+    const int64_t per = m->NE * ipow(Nf, m->dr);
+    const size_t vals = (size_t)nc * (size_t)per;
+    const bool ordered = n >= kEvalOrderMin;
+    const size_t ints = (size_t)nc + (ordered ? (size_t)(2 * m->NE + 3) + (size_t)n : 0);
+    void* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, vals * sizeof(float2) + ints * sizeof(int), st) != cudaSuccess)
+      return FP_ENOMEM;
+    float2* fs = (float2*)scratch;
+    int* emax = (int*)(fs + vals);
+    int* counts = emax + nc;              // [NE + 1]
+    int* start = counts + (m->NE + 1);    // [NE + 2]
+    int* perm = ordered ? start + (m->NE + 2) : nullptr;
+    const dim3 g((unsigned)grid_for(per, 256, 148 * 8), (unsigned)nc);
+    if (cudaMemsetAsync(emax, 0, (size_t)(ordered ? nc + m->NE + 1 : nc) * sizeof(int), st) != cudaSuccess)
+      rc = FP_ELAUNCH;
+    if (rc == FP_OK) {
+      k_field_exp<<<g, 256, 0, st>>>(field, per, emax);
+      k_field_split<<<g, 256, 0, st>>>(field, per, emax, fs);
+      if (ordered) {
+        const int pb = grid_for(n, 256, 148 * 8);
+        k_elem_count<<<pb, 256, 0, st>>>(code, elem, n, m->NE, counts);
+        // exclusive scan over the NE + 1 buckets (start[NE + 1] = n)
+        k_scan<<<1, 1024, 0, st>>>(counts, m->NE + 1, start);
+        k_elem_scatter<<<pb, 256, 0, st>>>(code, elem, n, m->NE, start, perm);
+      }
+      rc = dispatch_shape(Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+        constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;
+        (void)Dc;
+        const int blocks = grid_for(n, kEvalThreads, 148 * 64);
+        k_eval_df<N, DR><<<blocks, kEvalThreads, 0, st>>>(*B, code, elem, r, n, perm, fs, emax, nc, m->NE, out,
+                                                           m->status);
+        return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+      });
+    }
+    cudaFreeAsync(scratch, st);
+  } else {
+    rc = dispatch_shape(Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+      constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;
+      (void)Dc;
+      const int blocks = grid_for(n, kEvalThreads, 148 * 64);
+      k_eval_f64<N, DR><<<blocks, kEvalThreads, 0, st>>>(*B, code, elem, r, n, field, nc, m->NE, out,
+                                                          m->status);
+      return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+    });
+  }
   timer_span(m, FP_TIME_EVAL, t0, timer_mark(m, st));
   return rc;
 }

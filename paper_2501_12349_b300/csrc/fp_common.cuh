@@ -59,6 +59,12 @@ struct BasisTab {
   float wf[FP_MAX_N];
   float z2f[FP_MAX_N / 2];
   float w2f[FP_MAX_N];
+  // double-float forms (value = hi + lo, hi the FP32 rounding, lo the FP32
+  // rounding of the rest) of z, w and z^2 for the double-float interpolation
+  float zl[FP_MAX_N];
+  float wl[FP_MAX_N];
+  float z2h[FP_MAX_N / 2];
+  float z2l[FP_MAX_N / 2];
   double dn[FP_MAX_N * FP_MAX_N];  // dn[i * N + m] = phi_m'(z_i), the GLL differentiation matrix
 };
 

@@ -112,6 +112,12 @@ int host_basis_tab(int N, BasisTab* tab) {
   for (int m = 0; m < N / 2; ++m) {
     tab->z2[m] = tab->z[m] * tab->z[m];
     tab->z2f[m] = tab->zf[m] * tab->zf[m];
+    tab->z2h[m] = (float)tab->z2[m];
+    tab->z2l[m] = (float)(tab->z2[m] - (double)tab->z2h[m]);
+  }
+  for (int i = 0; i < N; ++i) {
+    tab->zl[i] = (float)(tab->z[i] - (double)tab->zf[i]);
+    tab->wl[i] = (float)(tab->w[i] - (double)tab->wf[i]);
   }
   // phi_m'(z_i) = (w_m / w_i) / (z_i - z_m) for m != i (differentiate the
   // product form of phi_m at a root of its other factors); the diagonal is
