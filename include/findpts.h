@@ -184,12 +184,15 @@ int fp_findpts_mixed_noalloc(fp_mesh m, const double* pts_dev, int64_t n, int32_
  * as the coordinates); 0 where code == FP_NOT_FOUND.  The same find output
  * serves any number of fields.
  * Precision follows the mesh's setting (fp_set_precision): FP_F64 contracts
- * in FP64; FP_MIXED contracts in double-float arithmetic on the FP32 pipe
- * (pairs of FP32 values with error-free transformations), within about
- * 1e-13 of the element's nodal scale of the FP64 result, and then takes
- * 8 bytes of device scratch per field value from the stream-ordered
- * allocator for the duration of the call (the field split into those
- * pairs after an exact power-of-two scaling per component).
+ * in FP64.  FP_MIXED, for quads, hexes and surfaces with n >= 16384 and
+ * n >= 8 NE, contracts in double-float arithmetic on the FP32 pipe (pairs
+ * of FP32 values with error-free transformations), within about 1e-13 of
+ * the element's nodal scale of the FP64 result, visiting the points in
+ * element order; it then takes 8 bytes of device scratch per field value
+ * (the field split into those pairs after an exact power-of-two scaling
+ * per component) plus 4 (n + 2 NE + nc + 3) bytes, from the stream-ordered
+ * allocator for the duration of the call.  Smaller FP_MIXED calls contract
+ * in FP64.
  * Errors: FP_EINVAL, FP_ENOMEM (FP_MIXED scratch), FP_ELAUNCH. */
 int fp_eval(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r,
             int64_t n, const double* field_dev, int nc, double* out, void* stream);

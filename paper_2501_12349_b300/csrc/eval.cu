@@ -16,7 +16,7 @@
 namespace fp {
 
 constexpr int kEvalThreads = 128;
-constexpr int64_t kEvalOrderMin = 16384;  // FP_MIXED: element order from this many points
+constexpr int64_t kEvalOrderMin = 16384;  // FP_MIXED: the double-float path from this many points
 
 template <int N, int DR>
 __global__ void __launch_bounds__(kEvalThreads)
@@ -206,12 +206,16 @@ int eval_impl(fp_mesh m, const int32_t* code, const int32_t* elem, const double*
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t t0 = timer_mark(m, st);
   int rc = FP_OK;
-  if (m->precision == FP_MIXED) {
+  // the double-float contraction pays once its per-point saving outweighs
+  // the per-call split of the field and the element sort: quads, hexes and
+  // surfaces, at least kEvalOrderMin points and 8 per element on average
+  const bool use_df = m->precision == FP_MIXED && m->dr >= 2 && n >= kEvalOrderMin && n >= 8 * m->NE;
+  if (use_df) {
     // scratch: the split field (a float pair per value), the exponents and,
     // for calls of kEvalOrderMin points or more, the element order
     const int64_t per = m->NE * ipow(Nf, m->dr);
     const size_t vals = (size_t)nc * (size_t)per;
-    const bool ordered = n >= kEvalOrderMin;
+    const bool ordered = true;
     const size_t ints = (size_t)nc + (ordered ? (size_t)(2 * m->NE + 3) + (size_t)n : 0);
     void* scratch = nullptr;
     if (cudaMallocAsync(&scratch, vals * sizeof(float2) + ints * sizeof(int), st) != cudaSuccess)
