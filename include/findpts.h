@@ -237,7 +237,11 @@ int fp_eval_order(fp_mesh m, const int32_t* code, const int32_t* elem, const dou
  * its FP64 pass) and one launch interpolates the items that carry a field.
  * The launches of all shapes are captured once into a CUDA graph on forked
  * streams; fp_batch_run replays that graph.  Pointers are captured: the
- * caller may change the point values between runs, not the buffers. */
+ * caller may change the point and field values between runs, not the
+ * buffers.  With FP_MIXED, a shape of quads, hexes or surfaces with the
+ * cell order and at least 8 points per element of its items with a field
+ * interpolates in double-float arithmetic (as fp_eval), its fields split
+ * on every run into plan-owned buffers (8 bytes per field value). */
 typedef struct {
   int mesh;              /* index into the meshes array given to fp_batch_create */
   const double* pts;     /* [n][d] device */
@@ -362,7 +366,11 @@ void fp_server_opts_default(fp_server_opts* opts);
 
 /* remap_fields[i] ([nc_remap[i]][NE][N^dr], device) and velocity[i]
  * ([d][NE][N^dr], device) may be NULL (arrays themselves may be NULL); they
- * must stay valid until fp_server_destroy.  Starts the scheduler thread. */
+ * must stay valid until fp_server_destroy.  With FP_MIXED the server
+ * interpolates on quads, hexes and surfaces in double-float arithmetic (as
+ * fp_eval) from copies of those fields split at creation (8 bytes of device
+ * memory per value): changes to the fields' contents after creation are not
+ * seen.  Starts the scheduler thread. */
 int fp_server_create(const fp_mesh* meshes, int nm, const double* const* remap_fields,
                      const int* nc_remap, const double* const* velocity,
                      const fp_server_opts* opts, fp_server* out);

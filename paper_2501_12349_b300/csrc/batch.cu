@@ -17,6 +17,7 @@
 #include <tuple>
 #include <vector>
 
+#include "eval_df.cuh"
 #include "find_common.cuh"
 
 namespace fp {
@@ -98,6 +99,14 @@ struct ClassPlan {
   int64_t buckets = 0;     // sum over items of (Psi_L cells + 1)
   bool unordered = false;  // some item's mesh takes its points as given
   bool has_field = false;
+  // FP_MIXED: double-float interpolation (the items' fields split on every
+  // run, in the point order), where it pays (see df_pays)
+  bool df = false;
+  float2* d_fs = nullptr;
+  int* d_fexp = nullptr;
+  SplitJob* d_jobs = nullptr;
+  int njobs = 0;
+  int64_t max_per = 0;
   Tuning tune;
   cudaStream_t side = nullptr;
   cudaEvent_t join = nullptr;
@@ -127,6 +136,23 @@ struct fp_batch_s {
 namespace fp {
 namespace {
 
+// The eval of one class: the double-float contraction over the class's
+// point order after splitting its fields (FP_MIXED, where it pays), else
+// the FP64 one in the items' order.
+int enqueue_eval(ClassPlan& c, cudaStream_t st) {
+  if (!c.has_field) return FP_OK;
+  if (!c.df) return launch_eval_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, st);
+  FP_CUDA_TRY(cudaMemsetAsync(c.d_fexp, 0, sizeof(int) * (size_t)c.njobs, st));
+  FP_TRY(split_fields(SplitJobs{c.d_jobs, nullptr, 0, nullptr, nullptr}, c.njobs, c.max_per, st));
+  return dispatch_shape(c.N, c.d, c.dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+    constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
+    (void)Dc;
+    k_eval_items_df<NN, DR><<<grid_for(c.total, 128, sm_count() * 16), 128, 0, st>>>(
+        c.d_items, (int)c.items.size(), c.total, c.d_order, c.B);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+  });
+}
+
 // Enqueues one class: counter reset, find launch(es), eval launch.
 int enqueue_class(ClassPlan& c, int precision, const Tuning& t, cudaStream_t st) {
   if (c.total == 0) return FP_OK;
@@ -137,8 +163,7 @@ int enqueue_class(ClassPlan& c, int precision, const Tuning& t, cudaStream_t st)
     FP_TRY(batch_cell_order(c.d_items, (int)c.items.size(), c.total, c.d, c.buckets, c.d_order, &order, st));
   FP_TRY(launch_batch_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, precision,
                             t.ctas_per_sm, t.clog2, order, c.d_queue, qcount, nullptr, st));
-  if (c.has_field) FP_TRY(launch_eval_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, st));
-  return FP_OK;
+  return enqueue_eval(c, st);
 }
 
 void destroy_graph(fp_batch_s* b) {
@@ -226,9 +251,7 @@ int capture_fused(fp_batch_s* b) {
     if (b->precision == FP_MIXED)
       FP_TRY(launch_batch_follow(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, c.d_queue,
                                  c.d_queue + c.total, c.side));
-    if (c.has_field)
-      FP_TRY(launch_eval_class(c.d_items, (int)c.items.size(), c.total, c.N, c.d, c.dr, c.B, c.side));
-    return FP_OK;
+    return enqueue_eval(c, c.side);
   });
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &g);
@@ -285,6 +308,9 @@ void free_plan(fp_batch_s* b) {
     cudaFree(c.d_items);
     cudaFree(c.d_queue);
     cudaFree(c.d_order);
+    cudaFree(c.d_fs);
+    cudaFree(c.d_fexp);
+    cudaFree(c.d_jobs);
     if (c.side) cudaStreamDestroy(c.side);
     if (c.join) cudaEventDestroy(c.join);
   }
@@ -384,6 +410,49 @@ extern "C" int fp_batch_create(const fp_mesh* meshes, int nm, const fp_batch_ite
         cudaMalloc(&c.d_order, sizeof(int) * (size_t)batch_cell_order_ints(c.total, c.buckets)) != cudaSuccess) {
       rc = FP_ENOMEM;
       break;
+    }
+    // FP_MIXED double-float interpolation where it pays: quads, hexes and
+    // surfaces in the point order, at least 8 points per element of the
+    // items with a field (the fields are split on every run)
+    if (precision == FP_MIXED && c.dr >= 2 && c.has_field && c.d_order) {
+      int64_t vals = 0, ne_sum = 0;
+      int nj = 0;
+      const int NN = ipow(c.N, c.dr);
+      for (const auto& it : c.items)
+        if (it.field) {
+          vals += (int64_t)it.nc * it.m.NE * NN;
+          ne_sum += it.m.NE;
+          nj += it.nc;
+        }
+      if (c.total >= 8 * ne_sum && nj > 0) {
+        if (cudaMalloc(&c.d_fs, sizeof(float2) * (size_t)vals) != cudaSuccess ||
+            cudaMalloc(&c.d_fexp, sizeof(int) * (size_t)nj) != cudaSuccess ||
+            cudaMalloc(&c.d_jobs, sizeof(SplitJob) * (size_t)nj) != cudaSuccess) {
+          rc = FP_ENOMEM;
+          break;
+        }
+        std::vector<SplitJob> jobs;
+        int64_t off = 0;
+        int eo = 0;
+        for (auto& it : c.items) {
+          if (!it.field) continue;
+          const int64_t per = it.m.NE * NN;
+          it.fs = c.d_fs + off;
+          it.fexp = c.d_fexp + eo;
+          for (int q = 0; q < it.nc; ++q)
+            jobs.push_back(SplitJob{it.field + q * per, per, c.d_fs + off + q * per, c.d_fexp + eo + q});
+          off += (int64_t)it.nc * per;
+          eo += it.nc;
+          c.max_per = std::max(c.max_per, per);
+        }
+        c.njobs = nj;
+        c.df = true;
+        if (cudaMemcpy(c.d_jobs, jobs.data(), sizeof(SplitJob) * jobs.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+          rc = FP_ELAUNCH;
+          break;
+        }
+      }
     }
     if (cudaMemcpyAsync(c.d_items, c.items.data(), sizeof(BatchItem) * c.items.size(),
                         cudaMemcpyHostToDevice, st) != cudaSuccess ||

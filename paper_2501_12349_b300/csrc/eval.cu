@@ -9,7 +9,7 @@
 // the coordinates); the kernel is the same with the GLL basis of N~ points.
 #include <mutex>
 
-#include "df64.cuh"
+#include "eval_df.cuh"
 #include "fp_basis.cuh"
 #include "fp_common.cuh"
 
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kEvalThreads)
 // With the mesh in mixed precision, interpolation runs on the FP32 pipe: the
 // field, scaled per component by an exact power of two so that its largest
 // magnitude lies in [1, 2), is split once per call into double-float pairs
-// (k_field_split), the bases are evaluated in double-float arithmetic from
+// (split_fields, eval_df.cuh), the bases are evaluated in double-float arithmetic from
 // the split r, and each stage of the sum-factorised contraction is a
 // compensated dot product of N terms (DfAcc).  Error: the input splits and
 // each double-float operation contribute about 2^-48 relative, each N-term
@@ -58,39 +58,6 @@ __global__ void __launch_bounds__(kEvalThreads)
 // |u_df - u| <= about 1e-13 of the element's nodal scale (at N <= 8, with the
 // Lebesgue constant's growth over the three stages), against the 1e-12 of
 // the interpolation tolerance; in practice a few 1e-16.
-
-// Per component c: the largest biased exponent of |field| (atomicMax).
-__global__ void k_field_exp(const double* __restrict__ field, int64_t per, int* __restrict__ emax) {
-  const int c = blockIdx.y;
-  const double* f = field + (int64_t)c * per;
-  int m = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x)
-    m = max(m, (int)((__double_as_longlong(f[i]) >> 52) & 0x7ff));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(emax + c, m);
-}
-
-// 2^(1023 - e) for a biased exponent e in [1, 2046], else 1 (an all-zero
-// component, or one holding an infinity or NaN, which propagates as in FP64).
-__device__ __forceinline__ double unscale_of(int e) {
-  return (e >= 1 && e <= 2046) ? __longlong_as_double((long long)(2046 - e) << 52) : 1.0;
-}
-__device__ __forceinline__ double scale_of(int e) {
-  return (e >= 1 && e <= 2046) ? __longlong_as_double((long long)e << 52) : 1.0;
-}
-
-// The field as (hi, lo) pairs, one 8-byte load per value as in FP64.
-__global__ void k_field_split(const double* __restrict__ field, int64_t per, const int* __restrict__ emax,
-                              float2* __restrict__ fs) {
-  const int c = blockIdx.y;
-  const double s = unscale_of(emax[c]);
-  const int64_t o = (int64_t)c * per;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
-    const df v = df_from(field[o + i] * s);  // exact scaling by a power of two
-    fs[o + i] = make_float2(v.h, v.l);
-  }
-}
 
 // Points in element order for the double-float contraction: counts per
 // element (bucket NE for the points not found), an exclusive scan, then
@@ -138,62 +105,94 @@ __global__ void __launch_bounds__(kEvalThreads)
 #pragma unroll
     for (int j = 0; j < DR; ++j) lagrange_sym_values_df<N>(B, df_from(__ldg(r + p * DR + j)), ph[j]);
     for (int c = 0; c < nc; ++c) {
-      const float2* x = fs + c * cs + (int64_t)e * NN;
-      auto ld = [&](int q) {
-        const float2 v = __ldg(x + q);
-        return df{v.x, v.y};
-      };
-      DfAcc acc;
-      if constexpr (DR == 3) {
-#pragma unroll 1
-        for (int k = 0; k < N; ++k) {
-          df pk = ph[2][0];
-#pragma unroll
-          for (int q = 1; q < N; ++q)
-            if (q == k) pk = ph[2][q];
-          DfAcc bk;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            DfAcc a;
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              const int q = (k * N + j) * N + i;
-              a.add(ld(q), ph[0][i]);
-            }
-            bk.add(a.get(), ph[1][j]);
-          }
-          acc.add(bk.get(), pk);
-        }
-      } else if constexpr (DR == 2) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          DfAcc a;
-#pragma unroll
-          for (int i = 0; i < N; ++i) a.add(ld(j * N + i), ph[0][i]);
-          acc.add(a.get(), ph[1][j]);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < N; ++i) acc.add(ld(i), ph[0][i]);
-      }
-      out[(int64_t)c * n + p] = df_to(acc.get()) * scale_of(__ldg(emax + c));
+      const df v = contract_df<N, DR>(fs + c * cs + (int64_t)e * NN, ph);
+      out[(int64_t)c * n + p] = df_to(v) * df_scale_of(__ldg(emax + c));
     }
   }
 }
 
 }  // namespace fp
 
-namespace {
+namespace fp {
 
 // GLL basis tables of every supported N, built once per process.
-const fp::BasisTab* basis_of(int N) {
-  static fp::BasisTab tabs[FP_MAX_N + 1];
+const BasisTab* basis_of(int N) {
+  static BasisTab tabs[FP_MAX_N + 1];
   static std::once_flag once;
   std::call_once(once, [] {
-    for (int k = 2; k <= FP_MAX_N; ++k) fp::host_basis_tab(k, &tabs[k]);
+    for (int k = 2; k <= FP_MAX_N; ++k) host_basis_tab(k, &tabs[k]);
   });
   return (N >= 2 && N <= FP_MAX_N) ? &tabs[N] : nullptr;
 }
+
+// The double-float contraction pays once its per-point saving outweighs the
+// per-call split of the field and the element sort: quads, hexes and
+// surfaces, at least kEvalOrderMin points and 8 per element on average.
+bool eval_uses_df(const fp_mesh_s* m, int64_t n) {
+  return m->precision == FP_MIXED && m->dr >= 2 && n >= kEvalOrderMin && n >= 8 * m->NE;
+}
+
+int df_field_prepare(const fp_mesh_s* m, const double* field, int Nf, int nc, DfField* f, cudaStream_t st) {
+  *f = DfField{};
+  const int64_t per = m->NE * ipow(Nf, m->dr);
+  const size_t vals = (size_t)nc * (size_t)per;
+  if (cudaMallocAsync(&f->scratch, vals * sizeof(float2) + (size_t)nc * sizeof(int), st) != cudaSuccess) {
+    f->scratch = nullptr;
+    return FP_ENOMEM;
+  }
+  f->fs = (float2*)f->scratch;
+  f->emax = (int*)(f->fs + vals);
+  f->nc = nc;
+  f->Nf = Nf;
+  FP_CUDA_TRY(cudaMemsetAsync(f->emax, 0, (size_t)nc * sizeof(int), st));
+  return split_fields(SplitJobs{nullptr, field, per, f->fs, f->emax}, nc, per, st);
+}
+
+int df_field_eval(const fp_mesh_s* m, const DfField& f, const int32_t* code, const int32_t* elem,
+                  const double* r, int64_t n, double* out, cudaStream_t st) {
+  if (n == 0) return FP_OK;
+  const BasisTab* B = f.Nf == m->N ? &m->basis : basis_of(f.Nf);
+  if (!B) return FP_EUNSUPPORTED;
+  // the element order (from kEvalOrderMin points; the order changes no value)
+  const bool ordered = n >= kEvalOrderMin;
+  int* ints = nullptr;
+  int* perm = nullptr;
+  if (ordered) {
+    if (cudaMallocAsync((void**)&ints, sizeof(int) * (size_t)(2 * m->NE + 3 + n), st) != cudaSuccess)
+      return FP_ENOMEM;
+    int* counts = ints;                 // [NE + 1]
+    int* start = counts + (m->NE + 1);  // [NE + 2]
+    perm = start + (m->NE + 2);
+    if (cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)(m->NE + 1), st) != cudaSuccess) {
+      cudaFreeAsync(ints, st);
+      return FP_ELAUNCH;
+    }
+    const int pb = grid_for(n, 256, 148 * 8);
+    k_elem_count<<<pb, 256, 0, st>>>(code, elem, n, m->NE, counts);
+    // exclusive scan over the NE + 1 buckets (start[NE + 1] = n)
+    k_scan<<<1, 1024, 0, st>>>(counts, m->NE + 1, start);
+    k_elem_scatter<<<pb, 256, 0, st>>>(code, elem, n, m->NE, start, perm);
+  }
+  const int rc = dispatch_shape(f.Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
+    constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;
+    (void)Dc;
+    const int blocks = grid_for(n, kEvalThreads, 148 * 64);
+    k_eval_df<N, DR><<<blocks, kEvalThreads, 0, st>>>(*B, code, elem, r, n, perm, f.fs, f.emax, f.nc, m->NE, out,
+                                                       m->status);
+    return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
+  });
+  if (ints) cudaFreeAsync(ints, st);
+  return rc;
+}
+
+void df_field_release(DfField& f, cudaStream_t st) {
+  if (f.scratch) cudaFreeAsync(f.scratch, st);
+  f = DfField{};
+}
+
+}  // namespace fp
+
+namespace {
 
 int eval_impl(fp_mesh m, const int32_t* code, const int32_t* elem, const double* r, int64_t n,
               const double* field, int Nf, int nc, double* out, void* stream) {
@@ -206,48 +205,11 @@ int eval_impl(fp_mesh m, const int32_t* code, const int32_t* elem, const double*
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t t0 = timer_mark(m, st);
   int rc = FP_OK;
-  // the double-float contraction pays once its per-point saving outweighs
-  // the per-call split of the field and the element sort: quads, hexes and
-  // surfaces, at least kEvalOrderMin points and 8 per element on average
-  const bool use_df = m->precision == FP_MIXED && m->dr >= 2 && n >= kEvalOrderMin && n >= 8 * m->NE;
-  if (use_df) {
-    // scratch: the split field (a float pair per value), the exponents and,
-    // for calls of kEvalOrderMin points or more, the element order
-    const int64_t per = m->NE * ipow(Nf, m->dr);
-    const size_t vals = (size_t)nc * (size_t)per;
-    const bool ordered = true;
-    const size_t ints = (size_t)nc + (ordered ? (size_t)(2 * m->NE + 3) + (size_t)n : 0);
-    void* scratch = nullptr;
-    if (cudaMallocAsync(&scratch, vals * sizeof(float2) + ints * sizeof(int), st) != cudaSuccess)
-      return FP_ENOMEM;
-    float2* fs = (float2*)scratch;
-    int* emax = (int*)(fs + vals);
-    int* counts = emax + nc;              // [NE + 1]
-    int* start = counts + (m->NE + 1);    // [NE + 2]
-    int* perm = ordered ? start + (m->NE + 2) : nullptr;
-    const dim3 g((unsigned)grid_for(per, 256, 148 * 8), (unsigned)nc);
-    if (cudaMemsetAsync(emax, 0, (size_t)(ordered ? nc + m->NE + 1 : nc) * sizeof(int), st) != cudaSuccess)
-      rc = FP_ELAUNCH;
-    if (rc == FP_OK) {
-      k_field_exp<<<g, 256, 0, st>>>(field, per, emax);
-      k_field_split<<<g, 256, 0, st>>>(field, per, emax, fs);
-      if (ordered) {
-        const int pb = grid_for(n, 256, 148 * 8);
-        k_elem_count<<<pb, 256, 0, st>>>(code, elem, n, m->NE, counts);
-        // exclusive scan over the NE + 1 buckets (start[NE + 1] = n)
-        k_scan<<<1, 1024, 0, st>>>(counts, m->NE + 1, start);
-        k_elem_scatter<<<pb, 256, 0, st>>>(code, elem, n, m->NE, start, perm);
-      }
-      rc = dispatch_shape(Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
-        constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;
-        (void)Dc;
-        const int blocks = grid_for(n, kEvalThreads, 148 * 64);
-        k_eval_df<N, DR><<<blocks, kEvalThreads, 0, st>>>(*B, code, elem, r, n, perm, fs, emax, nc, m->NE, out,
-                                                           m->status);
-        return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
-      });
-    }
-    cudaFreeAsync(scratch, st);
+  if (eval_uses_df(m, n)) {
+    DfField f;
+    rc = df_field_prepare(m, field, Nf, nc, &f, st);
+    if (rc == FP_OK) rc = df_field_eval(m, f, code, elem, r, n, out, st);
+    df_field_release(f, st);
   } else {
     rc = dispatch_shape(Nf, m->d, m->dr, [&](auto Nc, auto Dc, auto DRc) -> int {
       constexpr int N = decltype(Nc)::value, DR = decltype(DRc)::value;

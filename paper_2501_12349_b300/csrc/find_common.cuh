@@ -832,6 +832,8 @@ struct BatchItem {
   double* out;        // [nc] components, component c at out + c * ld
   int64_t ld;
   int64_t key_base;   // first of this item's order keys (order_keys of its mesh) in the batch's order
+  const float2* fs;   // FP_MIXED double-float interpolation: the field as (hi, lo) pairs, or NULL
+  const int* fexp;    // ... and its components' scaling exponents
 };
 
 // A batch of items of one element shape; the point sequence is the items'

@@ -174,6 +174,21 @@ int check_mesh(const fp_mesh_s* m);
 cudaEvent_t timer_mark(const fp_mesh_s* m, cudaStream_t st);
 void timer_span(const fp_mesh_s* m, int stage, cudaEvent_t a, cudaEvent_t b);
 void timer_free(fp_mesh_s* m);
+// The FP_MIXED double-float interpolation (eval.cu): whether a call of n
+// points takes it, and the field split once (df_field_prepare) for any
+// number of point sets (df_field_eval), released with df_field_release; all
+// stream-ordered on st.
+struct DfField {
+  float2* fs = nullptr;
+  int* emax = nullptr;
+  void* scratch = nullptr;
+  int nc = 0, Nf = 0;
+};
+bool eval_uses_df(const fp_mesh_s* m, int64_t n);
+int df_field_prepare(const fp_mesh_s* m, const double* field, int Nf, int nc, DfField* f, cudaStream_t st);
+int df_field_eval(const fp_mesh_s* m, const DfField& f, const int32_t* code, const int32_t* elem,
+                  const double* r, int64_t n, double* out, cudaStream_t st);
+void df_field_release(DfField& f, cudaStream_t st);
 }  // namespace fp
 
 #include <type_traits>

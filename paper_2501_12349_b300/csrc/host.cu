@@ -72,7 +72,13 @@ extern "C" int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int
     rc = FP_ELAUNCH;
   for (auto& e : ev)
     if (rc == FP_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = FP_ELAUNCH;
-  // the other streams start after the allocation on the caller's stream
+  // FP_MIXED interpolation in double float: decided for the whole call (so
+  // the values equal one fp_eval over all n points bit for bit) and the
+  // field split once, before the chunks
+  fp::DfField dff;
+  const bool df = nc > 0 && fp::eval_uses_df(m, n);
+  if (rc == FP_OK && df) rc = fp::df_field_prepare(m, field_dev, m->N, nc, &dff, st);
+  // the other streams start after the allocation (and the split) on the caller's stream
   if (rc == FP_OK && (cudaEventRecord(start, st) != cudaSuccess || cudaStreamWaitEvent(up, start, 0) != cudaSuccess ||
                       cudaStreamWaitEvent(down, start, 0) != cudaSuccess ||
                       cudaStreamWaitEvent(c1, start, 0) != cudaSuccess))
@@ -93,7 +99,9 @@ extern "C" int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int
     }
     rc = fp_findpts(m, pts + off * d, len, code + off, elem + off, r + off * dr, dist2 + off, cs);
     double* o = out + (size_t)nc * off;
-    if (rc == FP_OK && nc > 0) rc = fp_eval(m, code + off, elem + off, r + off * dr, len, field_dev, nc, o, cs);
+    if (rc == FP_OK && nc > 0)
+      rc = df ? fp::df_field_eval(m, dff, code + off, elem + off, r + off * dr, len, o, cs)
+              : fp_eval(m, code + off, elem + off, r + off * dr, len, field_dev, nc, o, cs);
     if (rc != FP_OK) break;
     if (cudaEventRecord(computed[k], cs) != cudaSuccess || cudaStreamWaitEvent(down, computed[k], 0) != cudaSuccess) {
       rc = FP_ELAUNCH;
@@ -116,6 +124,7 @@ extern "C" int fp_findpts_host(fp_mesh m, const double* pts_host, int64_t n, int
   if (up && cudaEventRecord(ev[2 * K + 2], up) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K + 2], 0);
   if (down && cudaEventRecord(ev[2 * K + 3], down) == cudaSuccess) cudaStreamWaitEvent(st, ev[2 * K + 3], 0);
   cudaFreeAsync(buf, st);
+  fp::df_field_release(dff, st);
   const cudaError_t es = cudaStreamSynchronize(st);
   if (rc == FP_OK && es != cudaSuccess) rc = FP_ELAUNCH;
   for (auto& e : ev)

@@ -40,6 +40,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "eval_df.cuh"
 #include "find_common.cuh"
 
 namespace fp {
@@ -198,7 +199,22 @@ struct MeshEntry {
   const double* remap_field;
   int nc_remap;
   const double* vel;
+  // FP_MIXED, quads/hexes/surfaces: the fields as double-float pairs (split
+  // at creation) and their components' scaling exponents
+  float2* remap_fs = nullptr;
+  int* remap_fexp = nullptr;
+  float2* vel_fs = nullptr;
+  int* vel_fexp = nullptr;
 };
+
+// The double-float copy of a resident field ([nc][NE][N^dr]): allocated and
+// split on stream st.
+int split_resident(const double* field, int nc, int64_t per, float2** fs, int** fexp, cudaStream_t st) {
+  FP_CUDA_TRY(cudaMalloc(fs, sizeof(float2) * (size_t)nc * (size_t)per));
+  FP_CUDA_TRY(cudaMalloc(fexp, sizeof(int) * (size_t)nc));
+  FP_CUDA_TRY(cudaMemsetAsync(*fexp, 0, sizeof(int) * (size_t)nc, st));
+  return split_fields(SplitJobs{nullptr, field, per, *fs, *fexp}, nc, per, st);
+}
 
 // A contiguous range of one request's points within one tick.
 struct Tile {
@@ -432,9 +448,13 @@ int launch_tick(fp_server_s* s, TickSlot& t) {
       if (q.kind == FP_REQ_REMAP) {
         bi.field = me.remap_field;
         bi.nc = me.remap_field ? me.nc_remap : 0;
+        bi.fs = me.remap_fs;
+        bi.fexp = me.remap_fexp;
       } else if (!last) {
         bi.field = me.vel;
         bi.nc = d;
+        bi.fs = me.vel_fs;
+        bi.fexp = me.vel_fexp;
       }
       bi.out = q.u + tl.off;
       bi.ld = q.n;
@@ -511,11 +531,20 @@ int enqueue_tick(fp_server_s* s, TickSlot& t, const std::vector<TickLaunch>& lau
       }
       FP_TRY(launch_batch_class(t.items_d + first, cnt, total, N, d, dr, m0->basis, s->opts.precision, 0, 5,
                                 order, qq, qq + total, nullptr, fs));
+      // FP_MIXED, quads, hexes and surfaces (fields split at creation): the
+      // double-float contraction, in the find's point order where the tick
+      // has one (the order changes no value: a request's result stays the
+      // same alone and in any mix); else the FP64 one
+      const bool df = s->opts.precision == FP_MIXED && dr >= 2;
       return dispatch_shape(N, d, dr, [&](auto Nc, auto Dc, auto DRc) -> int {
         constexpr int NN = decltype(Nc)::value, DR = decltype(DRc)::value;
         (void)Dc;
-        k_serve_eval<NN, DR><<<grid_for(total, 128, sm_count() * 16), 128, 0, fs>>>(t.items_d + first, cnt, total,
-                                                                                  m0->basis);
+        if (df)
+          k_eval_items_df<NN, DR><<<grid_for(total, 128, sm_count() * 16), 128, 0, fs>>>(t.items_d + first, cnt,
+                                                                                       total, order, m0->basis);
+        else
+          k_serve_eval<NN, DR><<<grid_for(total, 128, sm_count() * 16), 128, 0, fs>>>(t.items_d + first, cnt, total,
+                                                                                    m0->basis);
         return cudaGetLastError() == cudaSuccess ? FP_OK : FP_ELAUNCH;
       });
     }();
@@ -701,6 +730,12 @@ int destroy_server(fp_server_s* s) {
   if (s->up) cudaStreamDestroy(s->up);
   if (s->down) cudaStreamDestroy(s->down);
   cudaFree(s->arena.base);
+  for (auto& me : s->meshes) {
+    cudaFree(me.remap_fs);
+    cudaFree(me.remap_fexp);
+    cudaFree(me.vel_fs);
+    cudaFree(me.vel_fexp);
+  }
   return FP_OK;
 }
 
@@ -756,6 +791,16 @@ extern "C" int fp_server_create(const fp_mesh* meshes, int nm, const double* con
                        (int64_t)(s->meshes.size() + 1) * 256;
   int rc = FP_OK;
   if (!s->arena.init(o.mem_budget)) rc = FP_ENOMEM;
+  if (rc == FP_OK && o.precision == FP_MIXED) {
+    // the double-float copies of the resident fields (quads, hexes, surfaces)
+    for (auto& me : s->meshes) {
+      if (rc != FP_OK || me.m->dr < 2) continue;
+      const int64_t per = me.m->NE * (int64_t)me.m->ne;
+      if (me.remap_field) rc = split_resident(me.remap_field, me.nc_remap, per, &me.remap_fs, &me.remap_fexp, 0);
+      if (rc == FP_OK && me.vel) rc = split_resident(me.vel, me.m->d, per, &me.vel_fs, &me.vel_fexp, 0);
+    }
+    if (rc == FP_OK && cudaStreamSynchronize(0) != cudaSuccess) rc = FP_ELAUNCH;
+  }
   if (rc == FP_OK && (cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking) != cudaSuccess ||
                       cudaStreamCreateWithFlags(&s->down, cudaStreamNonBlocking) != cudaSuccess))
     rc = FP_ELAUNCH;
