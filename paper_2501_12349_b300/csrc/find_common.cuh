@@ -342,43 +342,18 @@ __device__ __forceinline__ void node_coords(const BasisTab& B, int n, T (&r)[DR]
   }
 }
 
-// x and G at the GLL node nb of element e, the start r0 of Newton: the
-// Lagrange basis is a unit vector at a node, so x is the node's coordinates,
-// and column j of G is the derivative along the node's grid line in
-// direction j, an N-term sum with the differentiation matrix dn (row
-// dn + i*N, i the node's index in direction j).
-template <int N, int D, int DR>
-__device__ __forceinline__ void node_start(const DevMesh& m, int e, int nb, const double* __restrict__ dn,
-                                           double (&x)[D], double (&G)[D * DR]) {
-  constexpr int NN = ipow(N, DR);
-  const double* X = m.coords + (int64_t)e * NN;
-  const int64_t cs = m.cstride;
-  const int idx[3] = {nb % N, (nb / N) % N, nb / (N * N)};
-#pragma unroll
-  for (int c = 0; c < D; ++c) x[c] = __ldg(X + c * cs + nb);
-#pragma unroll
-  for (int j = 0; j < DR; ++j) {
-    const int st = j == 0 ? 1 : (j == 1 ? N : N * N);
-    const double* line = X + (nb - idx[j] * st);
-    const double* row = dn + idx[j] * N;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      double g = 0.0;
-#pragma unroll
-      for (int k = 0; k < N; ++k) g = fma(__ldg(line + c * cs + k * st), row[k], g);
-      G[c * DR + j] = g;
-    }
-  }
-}
-
-// node_start for every lane of a converged warp that wants it, the warp
-// sharing the work: the D * DR entries of G of all starting lanes are tasks
-// spread over the 32 lanes (one N-term sum each, the same chain of FMAs in
-// the same order as node_start, so the result is bit-identical), written to
-// the owner's column of sg ([D * DR][kFindThreads]) and read back by it.
-// sl ([kFindThreads]) holds the warp's starting lanes by rank.  A lane
-// starting alone would otherwise charge the FP64 pipe all D * DR * N FMAs
-// of its node start as full-warp instructions.
+// x and G at the GLL node nb of element e, the start r0 of Newton, for
+// every lane of a converged warp that wants it: the Lagrange basis is a unit
+// vector at a node, so x is the node's coordinates, and column j of G is the
+// derivative along the node's grid line in direction j, an N-term sum with
+// the differentiation matrix dn (row dn + i*N, i the node's index in
+// direction j).  The warp shares the work: the D * DR entries of G of all
+// starting lanes are tasks spread over the 32 lanes (one N-term FMA chain
+// each, in the order of the nodes along the line), written to the owner's
+// column of sg ([D * DR][kFindThreads]) and read back by it; sl
+// ([kFindThreads]) holds the warp's starting lanes by rank.  A lane that
+// formed its own entries would charge the FP64 pipe all D * DR * N FMAs of
+// its start as full-warp instructions.
 template <int N, int D, int DR>
 __device__ __forceinline__ void node_start_warp(bool want, const DevMesh& m, int e, int nb,
                                                 const double* __restrict__ dn, double* sg, int* sl,

@@ -54,23 +54,6 @@ __device__ __forceinline__ void lagrange(const T* z, const T* w, T r, T* phi, T*
   }
 }
 
-// Values only: phi_i(r) = w_i (prefix product)_i (suffix product)_i.
-template <int N, typename T>
-__device__ __forceinline__ void lagrange_values(const T* z, const T* w, T r, T* phi) {
-  T d[N], p[N];
-#pragma unroll
-  for (int m = 0; m < N; ++m) d[m] = r - z[m];
-  p[0] = T(1);
-#pragma unroll
-  for (int i = 1; i < N; ++i) p[i] = p[i - 1] * d[i - 1];
-  T s = T(1);
-#pragma unroll
-  for (int i = N - 1; i >= 0; --i) {
-    phi[i] = w[i] * (p[i] * s);
-    s = s * d[i];
-  }
-}
-
 // The same bases by the symmetry of the GLL nodes (z_{N-1-i} = -z_i): with
 // s = r^2 and f_m = s - z_m^2 for the K = N/2 pairs, (r - z_i)(r + z_i) = f_i,
 // so the node polynomial is [r] prod_m f_m ([r] only for odd N) and
@@ -205,33 +188,6 @@ __device__ __forceinline__ void lagrange_sym_values(const BasisTab& B, T r, T* p
     }
   }
   if constexpr (kOdd) phi[K] = w[K] * ((K == 1) ? f[0] : L[0] * f[0]);
-}
-
-// Values, first and second derivatives.
-template <int N, typename T>
-__device__ __forceinline__ void lagrange2(const T* z, const T* w, T r, T* phi, T* dphi, T* d2phi) {
-  T d[N], p[N], dp[N], d2p[N];
-#pragma unroll
-  for (int m = 0; m < N; ++m) d[m] = r - z[m];
-  p[0] = T(1);
-  dp[0] = T(0);
-  d2p[0] = T(0);
-#pragma unroll
-  for (int i = 1; i < N; ++i) {
-    d2p[i] = fma(d2p[i - 1], d[i - 1], T(2) * dp[i - 1]);
-    dp[i] = fma(dp[i - 1], d[i - 1], p[i - 1]);
-    p[i] = p[i - 1] * d[i - 1];
-  }
-  T s = T(1), ds = T(0), d2s = T(0);
-#pragma unroll
-  for (int i = N - 1; i >= 0; --i) {
-    phi[i] = w[i] * (p[i] * s);
-    dphi[i] = w[i] * fma(dp[i], s, p[i] * ds);
-    d2phi[i] = w[i] * fma(d2p[i], s, fma(T(2) * dp[i], ds, p[i] * d2s));
-    d2s = fma(d2s, d[i], T(2) * ds);
-    ds = fma(ds, d[i], s);
-    s = s * d[i];
-  }
 }
 
 // x_c = sum u_ijk phi_i(r) phi_j(s) phi_k(t) for the D components of element
