@@ -52,9 +52,9 @@ KERNEL_SOURCES = {
 TRAFFIC = {
     # ncu -k regex:k_find_f64 -s 3 -c 1 (sections SpeedOfLight, MemoryWorkloadAnalysis, ...) on
     # bench.py --steps 2 --warmup 3 --skip-mixed --skip-batch --skip-serve --no-cpu-baseline
-    "k_find_f64": {"sha": "418fb442e0df1d78", "bytes": 732567040 + 74635008},
+    "k_find_f64": {"sha": "418e8f1cd0853b7a", "bytes": 734606592 + 75007488},
     # the same with --precision mixed and -k regex:k_find_mixed
-    "k_find_mixed": {"sha": "0a545319f709ef5e", "bytes": 535655680 + 68735744},
+    "k_find_mixed": {"sha": "04ecbeef635d6cf7", "bytes": 537254400 + 69029888},
 }
 
 
