@@ -6,7 +6,8 @@ and within 1e-13 of that scale of the FP64 kernel's, the error bound of the
 double-float contraction.  The nodal values are random (no smoothness, so
 the Lebesgue constant's growth over the three stages is met in full), the
 components are scaled by 1, 1e200 and 1e-200 (the per-component power-of-two
-scaling keeps every value in the FP32 range), and the element types are
+scaling keeps every value in the FP32 range) plus one all-zero component, and
+the element types are
 quads, hexes (order 7 on strongly deformed elements too), surface quads and
 line elements (which keep the FP64 contraction), plus a field of another
 order."""
@@ -43,9 +44,10 @@ def fp():
 
 
 def _field(rng, NE, Nf, dr):
-    f = rng.uniform(-1.0, 1.0, (3, NE, Nf ** dr))
+    f = rng.uniform(-1.0, 1.0, (4, NE, Nf ** dr))
     f[1] *= 1e200
     f[2] *= 1e-200
+    f[3] = 0.0  # no exponent at all: scaled by 1, interpolates to 0
     return np.ascontiguousarray(f)
 
 
@@ -80,6 +82,8 @@ def test_mixed_eval_matches_fp64_and_oracle(fp, torch, case):
         compare_eval(field, om.NE, ne, elem_in, uo, udf, f"{case} Nf={Nf} mixed eval vs oracle")
         e = np.where(elem_in >= 0, elem_in, 0)
         nodal = np.abs(field).max(axis=2)[:, e]
+        assert np.all(udf[3] == 0.0)
+        nodal[3] = 1.0
         err = np.abs(udf - u64) / np.maximum(nodal, np.abs(u64))
         assert np.all(udf[:, code == 2] == 0.0)
         assert err.max() <= 1e-13, (case, Nf, float(err.max()))
