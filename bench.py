@@ -45,16 +45,16 @@ WORKLOAD = "hex3d_32^3_p4_kershaw0.3_1e6pts"
 PKG_SRC = ROOT / "paper_2501_12349_b300" / "csrc"
 KERNEL_SOURCES = {
     "k_find_f64": ["find_f64.cuh", "find_common.cuh", "fp_basis.cuh", "beta_warp.cuh", "fp_common.cuh",
-                   "find.cu", "order.cu"],
-    "k_find_mixed": ["find_mixed.cu", "find_f64.cuh", "find_common.cuh", "fp_basis.cuh", "beta_warp.cuh",
-                     "fp_common.cuh", "find.cu", "order.cu"],
+                   "find.cu", "order.cu", "setup.cu"],
+    "k_find_mixed": ["find_mixed.cu", "find_mixed.cuh", "find_f64.cuh", "find_common.cuh", "fp_basis.cuh",
+                     "beta_warp.cuh", "fp_common.cuh", "find.cu", "order.cu", "setup.cu"],
 }
 TRAFFIC = {
     # ncu -k regex:k_find_f64 -s 3 -c 1 (sections SpeedOfLight, MemoryWorkloadAnalysis, ...) on
     # bench.py --steps 2 --warmup 3 --skip-mixed --skip-batch --skip-serve --no-cpu-baseline
-    "k_find_f64": {"sha": "418e8f1cd0853b7a", "bytes": 734606592 + 75007488},
+    "k_find_f64": {"sha": "5355243f03cff613", "bytes": 729354496 + 74311424},
     # the same with --precision mixed and -k regex:k_find_mixed
-    "k_find_mixed": {"sha": "04ecbeef635d6cf7", "bytes": 537254400 + 69029888},
+    "k_find_mixed": {"sha": "cc3e5d4ffc3f89d4", "bytes": 653602816 + 74608640},
 }
 
 

@@ -48,12 +48,12 @@ constexpr int kBetaScratch = 96;
 
 // The held set as newton_step defines it (g = -G^T dx; a coordinate on a
 // bound is held when the gradient points out of the box).
-template <int N, int D, int DR, typename T>
+template <int N, int D, int DR, typename T, int P = N>
 __device__ __forceinline__ BetaReq beta_request(bool want, const T (&r)[DR], const T (&dx)[D],
                                                 const T (&G)[D * DR]) {
   BetaReq q{BETA_NONE, 0, 0, 0, 0};
   if (!want) return q;
-  const int stride[3] = {1, N, N * N};
+  const int stride[3] = {1, P, P * N};
   int fr[DR];
   int nf = 0, base = 0;
   bool full = false;
@@ -143,9 +143,10 @@ __device__ __forceinline__ const T* shfl_ptr(const T* p, int src) {
 }
 
 // Called by all 32 lanes of a converged warp.  X, cs: this lane's element
-// data (component c at X + c*cs); scr: the warp's kBetaScratch values;
+// data (component c at X + c*cs, rows of N r-nodes at pitch P, as
+// beta_request's base assumes); scr: the warp's kBetaScratch values;
 // hs: [beta_entries][kFindThreads] values of the CTA.
-template <int N, int D, int DR, typename T>
+template <int N, int D, int DR, typename T, int P = N>
 __device__ void beta_warp(const BetaReq& q, const T* X, int64_t cs, const T (&r)[DR], const T (&dx)[D],
                           const BasisTab& B, T* scr, T* hs) {
   constexpr unsigned kAll = 0xffffffffu;
@@ -155,7 +156,7 @@ __device__ void beta_warp(const BetaReq& q, const T* X, int64_t cs, const T (&r)
   const T* z = TabOf<T>::z(B);
   const T* w = TabOf<T>::w(B);
   const T* w2 = TabOf<T>::w2(B);
-  const int stride[3] = {1, N, N * N};
+  const int stride[3] = {1, P, P * N};
 
   if (q.kind == BETA_ZERO) {
 #pragma unroll
@@ -266,7 +267,7 @@ __device__ void beta_warp(const BetaReq& q, const T* X, int64_t cs, const T (&r)
       T h[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
       for (int row = lane; row < N * N; row += 32) {
         const int j = row % N, k = row / N;
-        const T* xr = Xs + N * j + N * N * k;
+        const T* xr = Xs + P * j + P * N * k;
         T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
         for (int i = 0; i < N; ++i) {

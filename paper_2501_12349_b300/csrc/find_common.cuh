@@ -492,8 +492,9 @@ struct TSlots {
   __device__ __forceinline__ Slots<T> slot(int which) const { return Slots<T>{base + which * N * kFindThreads, kFindThreads}; }
 };
 
-// x(re) and, if WANT_G, G(re) of element data X: the uniform evaluation site.
-template <int N, int D, int DR, bool WANT_G, typename T>
+// x(re) and, if WANT_G, G(re) of element data X (rows at pitch P): the
+// uniform evaluation site.
+template <int N, int D, int DR, bool WANT_G, typename T, int P = N>
 __device__ __forceinline__ void eval_xG(const T* __restrict__ X, int64_t cs, const BasisTab& B,
                                         const T (&re)[DR], const TSlots<N, T>& ts, T* x, T* G) {
   T ph[3][N], dph[3][N];
@@ -514,7 +515,7 @@ __device__ __forceinline__ void eval_xG(const T* __restrict__ X, int64_t cs, con
       pt(k) = ph[2][k];
       dpt(k) = dph[2][k];
     }
-    map_eval_rolled<N, D, WANT_G, T>(X, cs, ph, dph, pt, dpt, x, G);
+    map_eval_rolled<N, D, WANT_G, T, P>(X, cs, ph, dph, pt, dpt, x, G);
   } else {
     T ph2[DR][N], dph2[DR][N];
 #pragma unroll
@@ -524,7 +525,7 @@ __device__ __forceinline__ void eval_xG(const T* __restrict__ X, int64_t cs, con
         ph2[j][i] = ph[j][i];
         dph2[j][i] = dph[j][i];
       }
-    map_eval<N, DR, D, WANT_G, T>(X, cs, ph2, dph2, x, G);
+    map_eval<N, DR, D, WANT_G, T, P>(X, cs, ph2, dph2, x, G);
   }
 }
 

@@ -163,6 +163,7 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
                                                 int* __restrict__ qcount, unsigned long long* stats,
                                                 MixedShared<N, D, DR>& sh) {
   constexpr int NN = ipow(N, DR);
+  constexpr int P32 = pitch32(N), NE32 = NN / N * P32;  // the padded FP32 copy
   float* const s_hs = sh.hs;
   float* const wscr = sh.bscr + (threadIdx.x >> 5) * kBetaScratch;
   const TSlots<N, double> ts64{sh.slab64};
@@ -423,7 +424,8 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
       for (int j = 0; j < DR; ++j) re[j] = (etype == X_TRIAL) ? rn[j] : r[j];
       float xv[D];
       if (etype != X_REST) ++cnt.v[7];
-      eval_xG<N, D, DR, true, float>(mp->coords32 + (int64_t)e * NN, mp->cstride, B, re, ts32, xv, G);
+      eval_xG<N, D, DR, true, float, P32>(mp->coords32p + (int64_t)e * NE32, mp->cstride32p, B, re, ts32, xv,
+                                          G);
       float Fn = 0.f;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
@@ -456,9 +458,10 @@ __device__ __forceinline__ void find_mixed_loop(const Work& w, const BasisTab& B
     // ---- warp-uniform beta term for the next FP32 Newton step ------------
     {
       const bool want = need && mode == X_NEWTON && l > 0 && at_bound<DR>(r);
-      const BetaReq bq = beta_request<N, D, DR, float>(want, r, dx, G);
+      const BetaReq bq = beta_request<N, D, DR, float, P32>(want, r, dx, G);
       if (__any_sync(0xffffffffu, bq.kind != BETA_NONE))
-        beta_warp<N, D, DR, float>(bq, mp->coords32 + (int64_t)e * NN, mp->cstride, r, dx, B, wscr, s_hs);
+        beta_warp<N, D, DR, float, P32>(bq, mp->coords32p + (int64_t)e * NE32, mp->cstride32p, r, dx, B, wscr,
+                                        s_hs);
     }
   }
   cnt.flush(stats);

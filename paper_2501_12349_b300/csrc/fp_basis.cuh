@@ -190,11 +190,56 @@ __device__ __forceinline__ void lagrange_sym_values(const BasisTab& B, T r, T* p
   if constexpr (kOdd) phi[K] = w[K] * ((K == 1) ? f[0] : L[0] * f[0]);
 }
 
+// One row of element data (N r-nodes from xe) contracted with the r-basis:
+// a += sum_i v_i phi_i and, if WANT_G, b += sum_i v_i phi_i', FMAs in
+// ascending i.  With kVec (FP32 rows padded to a multiple of 4 floats, so
+// xe is 16-byte aligned) the row first loads as float4s, then a float2 or
+// float for the rest: one or two load requests where N scalar loads would
+// be N; otherwise each value loads beside its FMAs.
+template <int N, bool kVec, bool WANT_G, typename T>
+__device__ __forceinline__ void row_dot(const T* __restrict__ xe, const T (&ph)[N], const T (&dph)[N], T& a,
+                                        T& b) {
+  if constexpr (kVec) {
+    static_assert(sizeof(T) == 4, "vector rows hold floats");
+    constexpr int kQ = (N % 4 == 3) ? (N + 3) / 4 : N / 4;  // float4s (a 3-rest takes one too)
+    T v[N];
+    const float4* q = reinterpret_cast<const float4*>(xe);
+#pragma unroll
+    for (int k = 0; k < kQ; ++k) {
+      const float4 f = __ldg(q + k);
+      const float t4[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (4 * k + t < N) v[4 * k + t] = t4[t];
+    }
+    if constexpr (N % 4 == 2) {
+      const float2 f = __ldg(reinterpret_cast<const float2*>(xe) + 2 * kQ);
+      v[N - 2] = f.x;
+      v[N - 1] = f.y;
+    } else if constexpr (N % 4 == 1) {
+      v[N - 1] = __ldg(reinterpret_cast<const float*>(xe) + N - 1);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      a = fma(v[i], ph[i], a);
+      if (WANT_G) b = fma(v[i], dph[i], b);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const T v = ldg(xe + i);
+      a = fma(v, ph[i], a);
+      if (WANT_G) b = fma(v, dph[i], b);
+    }
+  }
+}
+
 // x_c = sum u_ijk phi_i(r) phi_j(s) phi_k(t) for the D components of element
-// data X (component c at X + c*cs) and, if WANT_G, G[c*DR + j] = dx_c/dr_j.
-// Contraction order: r (the contiguous index) first, then s, then t, so a
-// component costs N^2 (2N + 3) + 4N FMA with G (N^3 + N^2 + N without).
-template <int N, int DR, int D, bool WANT_G, typename T>
+// data X (component c at X + c*cs, rows of N r-nodes at pitch P) and, if
+// WANT_G, G[c*DR + j] = dx_c/dr_j.  Contraction order: r (the contiguous
+// index) first, then s, then t, so a component costs N^2 (2N + 3) + 4N FMA
+// with G (N^3 + N^2 + N without).
+template <int N, int DR, int D, bool WANT_G, typename T, int P = N>
 __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, const T (&ph)[DR][N],
                                          const T (&dph)[DR][N], T* x, T* G) {
 #pragma unroll
@@ -208,12 +253,7 @@ __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, co
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           T a = T(0), b = T(0);
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const T v = ldg(xe + (k * N + j) * N + i);
-            a = fma(v, ph[0][i], a);
-            if (WANT_G) b = fma(v, dph[0][i], b);
-          }
+          row_dot<N, false, WANT_G, T>(xe + (k * N + j) * P, ph[0], dph[0], a, b);
           ak = fma(a, ph[1][j], ak);
           if (WANT_G) {
             bk = fma(b, ph[1][j], bk);
@@ -231,12 +271,7 @@ __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, co
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         T a = T(0), b = T(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const T v = ldg(xe + j * N + i);
-          a = fma(v, ph[0][i], a);
-          if (WANT_G) b = fma(v, dph[0][i], b);
-        }
+        row_dot<N, false, WANT_G, T>(xe + j * P, ph[0], dph[0], a, b);
         xv = fma(a, ph[1][j], xv);
         if (WANT_G) {
           g0 = fma(b, ph[1][j], g0);
@@ -244,12 +279,7 @@ __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, co
         }
       }
     } else {  // line elements
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const T v = ldg(xe + i);
-        xv = fma(v, ph[0][i], xv);
-        if (WANT_G) g0 = fma(v, dph[0][i], g0);
-      }
+      row_dot<N, false, WANT_G, T>(xe, ph[0], dph[0], xv, g0);
     }
     x[c] = xv;
     if (WANT_G) {
@@ -269,14 +299,18 @@ struct Slots {
   __device__ __forceinline__ T& operator()(int k) const { return base[k * stride + threadIdx.x]; }
 };
 
-// As map_eval for hexes (DR == 3), with the outer t-loop rolled: the t-basis
-// values come from shared-memory slots pt(k) = phi_k(t), dpt(k) = phi_k'(t),
-// so the contraction inlines as one N^2 body instead of N^3 (a much smaller
-// kernel: the FP64 find kernels were instruction-fetch bound unrolled).
-template <int N, int D, bool WANT_G, typename T>
+// As map_eval for hexes (DR == 3, rows at pitch P), with the outer t-loop
+// rolled: the t-basis values come from shared-memory slots pt(k) = phi_k(t),
+// dpt(k) = phi_k'(t), so the contraction inlines as one N^2 body instead of
+// N^3 (a much smaller kernel: the FP64 find kernels were instruction-fetch
+// bound unrolled).  FP32 rows at a pitch that is a multiple of 4 load as
+// vectors (in the unrolled map_eval of quads and surfaces, the vector loads
+// of all rows held at once spill at high order, so rows load as scalars).
+template <int N, int D, bool WANT_G, typename T, int P = N>
 __device__ __forceinline__ void map_eval_rolled(const T* __restrict__ X, int64_t cs,
                                                 const T (&ph)[3][N], const T (&dph)[3][N],
                                                 const Slots<T>& pt, const Slots<T>& dpt, T* x, T* G) {
+  constexpr bool kVec = sizeof(T) == 4 && P % 4 == 0;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const T* xe = X + c * cs;
@@ -287,12 +321,7 @@ __device__ __forceinline__ void map_eval_rolled(const T* __restrict__ X, int64_t
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         T a = T(0), b = T(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const T v = ldg(xe + (k * N + j) * N + i);
-          a = fma(v, ph[0][i], a);
-          if (WANT_G) b = fma(v, dph[0][i], b);
-        }
+        row_dot<N, kVec, WANT_G, T>(xe + (k * N + j) * P, ph[0], dph[0], a, b);
         ak = fma(a, ph[1][j], ak);
         if (WANT_G) {
           bk = fma(b, ph[1][j], bk);

@@ -68,11 +68,19 @@ struct BasisTab {
   double dn[FP_MAX_N * FP_MAX_N];  // dn[i * N + m] = phi_m'(z_i), the GLL differentiation matrix
 };
 
+// Row pitch of the padded FP32 coordinate copy: a row of N r-nodes padded
+// to a multiple of 4 floats, so every row starts on a 16-byte boundary and
+// loads as whole float4s (for N = 5..8 one 32-byte sector per row); ne32p =
+// pitch32(N) N^(dr-1) floats per element and component.
+__host__ __device__ constexpr int pitch32(int N) { return (N + 3) & ~3; }
+
 // Everything a find / eval kernel reads about a mesh (passed by value).
 struct DevMesh {
   const double* coords;    // [d][NE][ne]
   const float* coords32;   // FP32 copy relative to the element reference point
                            // (elem_ref): fl(x - x_ref), so values are O(h)
+  const float* coords32p;  // [d][NE][ne32p]: coords32 with each row of N r-nodes padded
+                           // with zeros to pitch32(N) floats (the FP32 Newton phase)
   const double* aabb;      // [NE][2d], expanded
   const double* obb_c;     // [NE][d]
   const double* obb_A;     // [NE][d][d]
@@ -84,6 +92,7 @@ struct DevMesh {
   const int* cell_elems;   // [nnz]
   int64_t NE;
   int64_t cstride;         // NE * ne: distance between coordinate components
+  int64_t cstride32p;      // NE * ne32p: the same in coords32p
   double lo[3], hi[3], scale[3];
   int NL;
   int max_iter;
@@ -150,6 +159,7 @@ struct fp_mesh_s {
   int precision;
   double* coords;
   float* coords32;
+  float* coords32p;
   double* aabb;
   double* obb_c;
   double* obb_A;

@@ -767,6 +767,22 @@ __global__ void k_coords32(const double* __restrict__ x, const double* __restric
   }
 }
 
+// coords32p[c][e][row P + i] = coords32[c][e][row N + i] for i < N, 0 in the
+// pad i = N..P-1 (P = pitch32(N), rows = N^(dr-1)).
+__global__ void k_coords32p(const float* __restrict__ x32, int64_t nce, int N, int rows,
+                            float* __restrict__ y) {
+  const int P = pitch32(N);
+  const int ne = N * rows, ne32p = P * rows;
+  const int64_t total = nce * ne32p;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ce = o / ne32p;
+    const int q = (int)(o - ce * ne32p);
+    const int row = q / P, i = q - row * P;
+    y[o] = (i < N) ? x32[ce * ne + row * N + i] : 0.f;
+  }
+}
+
 // FP32 record per element (layout fp::BOX32): lo[3] hi[3] c[3] A[3][3] Xrel
 // pad xc[3] T[3][3], rounded to nearest (the certified FP32 tests carry
 // their own margins); Xrel = largest AABB half-width, slightly enlarged,
@@ -895,6 +911,7 @@ void free_mesh_memory(fp_mesh_s* m) {
   timer_free(m);
   cudaFree(m->coords);
   cudaFree(m->coords32);
+  cudaFree(m->coords32p);
   cudaFree(m->aabb);
   cudaFree(m->obb_c);
   cudaFree(m->obb_A);
@@ -914,6 +931,7 @@ fp::DevMesh fp_mesh_s::view() const {
   fp::DevMesh v;
   v.coords = coords;
   v.coords32 = coords32;
+  v.coords32p = coords32p;
   v.aabb = aabb;
   v.obb_c = obb_c;
   v.obb_A = obb_A;
@@ -923,6 +941,7 @@ fp::DevMesh fp_mesh_s::view() const {
   v.cell_elems = cell_elems;
   v.NE = NE;
   v.cstride = NE * (int64_t)ne;
+  v.cstride32p = NE * (int64_t)(fp::pitch32(N) * fp::ipow(N, dr - 1));
   for (int c = 0; c < 3; ++c) {
     v.lo[c] = lo[c];
     v.hi[c] = hi[c];
@@ -1161,10 +1180,12 @@ extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int6
   m->precision = o.precision;
   host_basis_tab(N, &m->basis);
   const size_t nc = (size_t)d * NE * m->ne;
+  const size_t nc32p = (size_t)d * NE * (pitch32(N) * ipow(N, dr - 1));
   int rc = FP_OK;
   do {
     if ((rc = dev_alloc(&m->coords, nc, &m->bytes)) != FP_OK) break;
     if ((rc = dev_alloc(&m->coords32, nc, &m->bytes)) != FP_OK) break;
+    if ((rc = dev_alloc(&m->coords32p, nc32p, &m->bytes)) != FP_OK) break;
     if ((rc = dev_alloc(&m->aabb, (size_t)NE * 2 * d, &m->bytes)) != FP_OK) break;
     if ((rc = dev_alloc(&m->obb_c, (size_t)NE * d, &m->bytes)) != FP_OK) break;
     if ((rc = dev_alloc(&m->obb_A, (size_t)NE * d * d, &m->bytes)) != FP_OK) break;
@@ -1180,6 +1201,8 @@ extern "C" int fp_setup(const double* coords_dev, int d, int dr, int order, int6
     if ((rc = build_boxes_and_grid(m, st)) != FP_OK) break;
     k_coords32<<<grid_for((int64_t)nc, 256, 148 * 16), 256, 0, st>>>(m->coords, m->aabb, d, NE, m->ne,
                                                                     m->coords32);
+    k_coords32p<<<grid_for((int64_t)nc32p, 256, 148 * 16), 256, 0, st>>>(m->coords32, (int64_t)d * NE, N,
+                                                                        ipow(N, dr - 1), m->coords32p);
     int hstat = 0;
     if (cudaMemcpyAsync(&hstat, m->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {

@@ -61,7 +61,7 @@ def test_mixed_cases(fp, torch, case):
     m.close()
 
 
-@pytest.mark.parametrize("order", [1, 2, 3, 5, 7])
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("shape", ["quad2d", "hex3d"])
 def test_mixed_every_order(fp, torch, shape, order):
     rng = np.random.default_rng(200 + order)
