@@ -52,9 +52,9 @@ KERNEL_SOURCES = {
 TRAFFIC = {
     # ncu -k regex:k_find_f64 -s 3 -c 1 (sections SpeedOfLight, MemoryWorkloadAnalysis, ...) on
     # bench.py --steps 2 --warmup 3 --skip-mixed --skip-batch --skip-serve --no-cpu-baseline
-    "k_find_f64": {"sha": "5355243f03cff613", "bytes": 729354496 + 74311424},
+    "k_find_f64": {"sha": "2c6e87d7009350f2", "bytes": 729277952 + 74185984},
     # the same with --precision mixed and -k regex:k_find_mixed
-    "k_find_mixed": {"sha": "cc3e5d4ffc3f89d4", "bytes": 653602816 + 74608640},
+    "k_find_mixed": {"sha": "1880c1ff13ae6897", "bytes": 653234176 + 74882304},
 }
 
 

@@ -242,6 +242,9 @@ __device__ __forceinline__ void row_dot(const T* __restrict__ xe, const T (&ph)[
 template <int N, int DR, int D, bool WANT_G, typename T, int P = N>
 __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, const T (&ph)[DR][N],
                                          const T (&dph)[DR][N], T* x, T* G) {
+  // vector rows for FP32 lines, and quads up to N = 5 (beyond it the
+  // unrolled contraction's rows, loaded ahead, spill)
+  constexpr bool kVec = sizeof(T) == 4 && P % 4 == 0 && (DR == 1 || (DR == 2 && N <= 5));
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const T* xe = X + c * cs;
@@ -271,7 +274,7 @@ __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, co
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         T a = T(0), b = T(0);
-        row_dot<N, false, WANT_G, T>(xe + j * P, ph[0], dph[0], a, b);
+        row_dot<N, kVec, WANT_G, T>(xe + j * P, ph[0], dph[0], a, b);
         xv = fma(a, ph[1][j], xv);
         if (WANT_G) {
           g0 = fma(b, ph[1][j], g0);
@@ -279,7 +282,7 @@ __device__ __forceinline__ void map_eval(const T* __restrict__ X, int64_t cs, co
         }
       }
     } else {  // line elements
-      row_dot<N, false, WANT_G, T>(xe, ph[0], dph[0], xv, g0);
+      row_dot<N, kVec, WANT_G, T>(xe, ph[0], dph[0], xv, g0);
     }
     x[c] = xv;
     if (WANT_G) {
@@ -304,8 +307,7 @@ struct Slots {
 // dpt(k) = phi_k'(t), so the contraction inlines as one N^2 body instead of
 // N^3 (a much smaller kernel: the FP64 find kernels were instruction-fetch
 // bound unrolled).  FP32 rows at a pitch that is a multiple of 4 load as
-// vectors (in the unrolled map_eval of quads and surfaces, the vector loads
-// of all rows held at once spill at high order, so rows load as scalars).
+// vectors.
 template <int N, int D, bool WANT_G, typename T, int P = N>
 __device__ __forceinline__ void map_eval_rolled(const T* __restrict__ X, int64_t cs,
                                                 const T (&ph)[3][N], const T (&dph)[3][N],

@@ -24,10 +24,12 @@ namespace {
 // Each chunk adds the tail of its find launch (a few tenths of a
 // millisecond, partly hidden by the other compute stream) and hides the
 // copies of all but the first upload and the last download (about 1.3 ms
-// per 10^6 points in and out).  Measured on the 32^3 p=4 hex mesh: two
-// chunks are best at 10^6 points (13.6 against 14.2 ms for one), three or
-// four at 4x10^6 (51.8 against 55.2 ms); so chunks of n/4 points, at least
-// 2^19.
+// per 10^6 points in and out).  Measured on the 32^3 p=4 hex mesh with one
+// field (find, eval and copies, L2 flushed before each call): at 10^6
+// points two chunks are best, FP64 9.65 ms against 10.19 for one and 9.75,
+// 9.89, 10.21 for three, four, five; FP_MIXED 3.76 against 3.87, 3.79,
+// 3.87, 4.18; at 4x10^6 three or four were best (51.8 against 55.2 ms for
+// one, an earlier FP64 kernel); so chunks of n/4 points, at least 2^19.
 int64_t auto_chunk(int64_t n) {
   const int64_t c = (n + 3) / 4;
   return c < ((int64_t)1 << 19) ? ((int64_t)1 << 19) : c;
