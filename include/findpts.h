@@ -103,8 +103,14 @@ void fp_opts_default(fp_opts* opts);
 
 /* Setup (Sec. 3.1).  Copies coords_dev ([d][NE][N^dr] FP64, device) into
  * library-owned device memory, computes element AABBs and OBBs expanded by
- * bbox_tol and builds Psi_L, all on the GPU.  Blocks until done (it
- * allocates).  *out receives the handle; fp_free releases it.
+ * bbox_tol and builds Psi_L, all on the GPU.  Besides the FP64 copy the mesh
+ * keeps two FP32 copies of the coordinates relative to each element's
+ * centre (one with its rows of N nodes padded to 16-byte boundaries, for
+ * the mixed path's vector loads) and per-element box and curvature records:
+ * per coordinate value 8 + 4 + 4 P/N bytes (P = 4 ceil(N/4), so 18.4 bytes
+ * at N = 5), plus about 0.3 KB per element; fp_mesh_info reports the total.
+ * Blocks until done (it allocates).  *out receives the handle; fp_free
+ * releases it.
  * Errors: FP_EINVAL for a bad dimension pair, order, NE <= 0 or M outside
  * [2, 32]; FP_EUNSUPPORTED for N > FP_MAX_N; FP_ENOMEM; FP_ELAUNCH. */
 int fp_setup(const double* coords_dev, int d, int dr, int order, int64_t NE,
